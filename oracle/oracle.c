@@ -1,0 +1,875 @@
+/*
+ * oracle.c -- plain, slow, FP64 CPU reference for Monte-Carlo scattering
+ * tomography with path recycling (Czerninski & Schechner, "Accelerating
+ * Inverse Rendering By Using a GPU and Reuse of Light Paths", arXiv
+ * 2110.00085).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library path links, loads or
+ * calls this file; only the tests, the package's smoke check and the
+ * benchmark's CPU-baseline leg do.  It shares no code, header, table or
+ * constant with the CUDA implementation: the random-number generator,
+ * voxel traversal, phase functions, camera model and estimators below are
+ * written from their published definitions.
+ *
+ * What it computes, in the paper's order and notation:
+ *   - forward path tracing through a voxel extinction grid with a
+ *     directional sun (Sec. 3.4; sun with parallel rays, Sec. 6.1):
+ *     distance sampling by inverting the transmittance (Sec. 3.4.1),
+ *     particle-type choice then direction sampling (Sec. 3.4.2);
+ *   - local estimation toward every camera pixel (Sec. 3.4.3, Eq. Qd);
+ *   - the path-recycling estimator F(M_t | M_ref), i.e. f(x|M_t) over
+ *     mu(x|M_ref) for paths sampled under M_ref (Sec. 5.2, Eqs. 19-21);
+ *     with M_t = M_ref it is the plain estimator of Eq. (forward_simulation);
+ *   - the loss gradient sum_d (F_d - I_d) dF_d/dbeta_v with the path score
+ *     function of scattering tomography (Sec. 4.4 and Appendix C, the
+ *     equation closing Sec. C.1), evaluated term by term per event.
+ *
+ * Readings where the paper is silent or inconsistent are marked READING.
+ * Parity status: every function here is pinned by the CPU test suite
+ * (closed forms, invariants, quadrature, finite differences, brute force);
+ * multiple-scattering images beyond first order have no closed form and are
+ * pinned only through energy balance, unbiasedness and the FD identity.
+ *
+ * Floating point: all path arithmetic is double.  Build with
+ * -ffp-contract=off so results do not depend on the host's FMA contraction.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.14159265358979323846
+#define OR_MAXV 64        /* vertices kept per path (max_orders + 1) */
+
+/* tallies (doubles) */
+enum {
+    T_INJECTED = 0,   /* w0 of paths that entered the box               */
+    T_MISSED,         /* w0 of paths that missed the box                */
+    T_ESCAPED,        /* weight leaving the box                         */
+    T_ABSORBED,       /* w (1 - albedo) at every collision              */
+    T_TRUNCATED,      /* weight after the last allowed order            */
+    T_RR_KILLED,      /* weight of paths ended by Russian roulette      */
+    T_RR_GAIN,        /* weight added by the 1/q survival boost         */
+    T_COLLISIONS,     /* number of collisions                           */
+    T_ENTERED,        /* number of paths that entered the box           */
+    T_SEG_CROSS,      /* voxel intervals crossed by sampled flights     */
+    T_SHADOW_CROSS,   /* voxel intervals crossed by in-view shadow rays */
+    T_IN_VIEW,        /* local estimates that landed in a pixel         */
+    T_COUNT
+};
+
+/* event types of a path end */
+enum { END_NONE = 0, END_ESCAPE = 1, END_TRUNC = 2, END_RR = 3, END_MISS = 4 };
+
+/* ------------------------------------------------------------------------ */
+/* scene description (filled from Python through ctypes)                   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t nx, ny, nz, n_cams;
+    int32_t max_orders, rr_start;
+    uint32_t epoch, scene_id;
+    uint64_t seed;
+    double voxel;                /* km, cubic voxels                        */
+    double origin[3];
+    double beta_air, albedo_cloud, albedo_air, hg_g;
+    double sun[3];               /* unit propagation direction              */
+    double sun_irradiance;
+    double rr_q;
+    const double* cams;          /* n_cams x 12: pos, look_at, up, fov_y, W, H */
+} or_scene;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the      */
+/* multiply-xor bijection with Weyl-sequence key schedule.                  */
+/* ------------------------------------------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t x0 = ctr_in[0], x1 = ctr_in[1], x2 = ctr_in[2], x3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += W0; k1 += W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* uniform on (0, 1]: the top 24 bits plus one, times 2^-24 */
+static double u01(uint32_t x) { return (double)((x >> 8) + 1u) * (1.0 / 16777216.0); }
+
+/* Draw the 4 words of (path, event, tag).  Counter layout:
+ * (path lo, path hi, event | tag << 8 | epoch << 16, scene id); key = seed. */
+static void draw(const or_scene* s, uint64_t path, uint32_t event, uint32_t tag, double u[4])
+{
+    uint32_t ctr[4], key[2], w[4];
+    ctr[0] = (uint32_t)path;
+    ctr[1] = (uint32_t)(path >> 32);
+    ctr[2] = (event & 0xffu) | ((tag & 0xffu) << 8) | ((s->epoch & 0xffffu) << 16);
+    ctr[3] = s->scene_id;
+    key[0] = (uint32_t)s->seed;
+    key[1] = (uint32_t)(s->seed >> 32);
+    or_philox4x32_10(ctr, key, w);
+    for (int i = 0; i < 4; ++i) u[i] = u01(w[i]);
+}
+
+/* FNV-1a, 64 bit, over the little-endian bytes of 32-bit words */
+static uint64_t fnv_word(uint64_t h, uint32_t w)
+{
+    for (int i = 0; i < 4; ++i) {
+        h ^= (uint64_t)((w >> (8 * i)) & 0xffu);
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+uint64_t or_fnv1a_words(const uint32_t* w, int n)
+{
+    uint64_t h = 0xcbf29ce484222325ull;
+    for (int i = 0; i < n; ++i) h = fnv_word(h, w[i]);
+    return h;
+}
+
+/* ------------------------------------------------------------------------ */
+/* small vector helpers                                                      */
+/* ------------------------------------------------------------------------ */
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double a[3], const double b[3], double o[3])
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+static void normalize3(double a[3])
+{
+    double n = sqrt(dot3(a, a));
+    a[0] /= n; a[1] /= n; a[2] /= n;
+}
+
+/* Orthonormal basis around unit n (Duff et al., JCGT 6(1), 2017). */
+void or_onb(const double n[3], double b1[3], double b2[3])
+{
+    double sign = copysign(1.0, n[2]);
+    double a = -1.0 / (sign + n[2]);
+    double b = n[0] * n[1] * a;
+    b1[0] = 1.0 + sign * n[0] * n[0] * a; b1[1] = sign * b; b1[2] = -sign * n[0];
+    b2[0] = b; b2[1] = sign + n[1] * n[1] * a; b2[2] = -n[1];
+}
+
+/* ------------------------------------------------------------------------ */
+/* phase functions (Sec. 3.1.4): HG for cloud, Rayleigh for air.  Both are  */
+/* normalised over the sphere (Eq. phase_conservation); mu = cos(theta)     */
+/* between incoming and outgoing propagation directions.                    */
+/* ------------------------------------------------------------------------ */
+double or_phase_hg(double g, double mu)
+{
+    double den = 1.0 + g * g - 2.0 * g * mu;
+    return (1.0 - g * g) / (4.0 * OR_PI * den * sqrt(den));
+}
+double or_phase_rayleigh(double mu) { return 3.0 * (1.0 + mu * mu) / (16.0 * OR_PI); }
+
+/* inverse CDF of HG in mu (cdf increasing from mu=-1 at u->0 to mu=1 at u=1) */
+double or_sample_hg(double g, double u)
+{
+    if (fabs(g) < 1e-3) return 2.0 * u - 1.0;
+    double t = (1.0 - g * g) / (1.0 - g + 2.0 * g * u);
+    double mu = (1.0 + g * g - t * t) / (2.0 * g);
+    if (mu > 1.0) mu = 1.0;
+    if (mu < -1.0) mu = -1.0;
+    return mu;
+}
+/* inverse CDF of Rayleigh: cdf(mu) = (mu^3 + 3 mu + 4)/8, solved by Cardano */
+double or_sample_rayleigh(double u)
+{
+    double q = 4.0 * u - 2.0;
+    double w = cbrt(q + sqrt(q * q + 1.0));
+    double mu = w - 1.0 / w;
+    if (mu > 1.0) mu = 1.0;
+    if (mu < -1.0) mu = -1.0;
+    return mu;
+}
+
+/* rotate unit d by polar cosine mu and azimuth phi about itself */
+void or_rotate(const double d[3], double mu, double phi, double out[3])
+{
+    double b1[3], b2[3];
+    or_onb(d, b1, b2);
+    double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+    double c = cos(phi), s = sin(phi);
+    for (int i = 0; i < 3; ++i) out[i] = st * c * b1[i] + st * s * b2[i] + mu * d[i];
+}
+
+/* ------------------------------------------------------------------------ */
+/* grid geometry: a segment p + t d, t in [0, tmax], is cut by the voxel    */
+/* faces into intervals; each interval lies in exactly one voxel, which is  */
+/* the voxel containing its midpoint.  This is the set {l_{b,v}} of Sec.    */
+/* 4.4 (Fig. inverse_notations) computed by brute force: every face         */
+/* crossing is listed and the list sorted.                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct { int64_t v; double t0, t1; } ivl;
+
+static int cmp_double(const void* a, const void* b)
+{
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x < y) ? -1 : (x > y) ? 1 : 0;
+}
+
+/* clip [0, tmax] to the box; returns 0 when the segment misses it */
+static int clip_box(const or_scene* s, const double p[3], const double d[3], double tmax, double* ta, double* tb)
+{
+    const int n[3] = {s->nx, s->ny, s->nz};
+    double t0 = 0.0, t1 = tmax;
+    for (int a = 0; a < 3; ++a) {
+        double lo = s->origin[a], hi = s->origin[a] + n[a] * s->voxel;
+        if (d[a] == 0.0) {
+            if (p[a] < lo || p[a] > hi) return 0;
+            continue;
+        }
+        double u0 = (lo - p[a]) / d[a], u1 = (hi - p[a]) / d[a];
+        if (u0 > u1) { double tmp = u0; u0 = u1; u1 = tmp; }
+        if (u0 > t0) t0 = u0;
+        if (u1 < t1) t1 = u1;
+    }
+    if (!(t1 > t0)) return 0;
+    *ta = t0; *tb = t1;
+    return 1;
+}
+
+/* list the voxel intervals of p + t d on [0, tmax]; out must hold nx+ny+nz+4 */
+static int intervals(const or_scene* s, const double p[3], const double d[3], double tmax, ivl* out, double* tbuf)
+{
+    const int n[3] = {s->nx, s->ny, s->nz};
+    double ta, tb;
+    if (!clip_box(s, p, d, tmax, &ta, &tb)) return 0;
+    int m = 0;
+    tbuf[m++] = ta;
+    tbuf[m++] = tb;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) continue;
+        double c0 = (p[a] + ta * d[a] - s->origin[a]) / s->voxel;
+        double c1 = (p[a] + tb * d[a] - s->origin[a]) / s->voxel;
+        double lo = fmin(c0, c1), hi = fmax(c0, c1);
+        long k0 = (long)ceil(lo), k1 = (long)floor(hi);
+        if (k0 < 1) k0 = 1;
+        if (k1 > n[a] - 1) k1 = n[a] - 1;
+        for (long k = k0; k <= k1; ++k) {
+            double t = (s->origin[a] + (double)k * s->voxel - p[a]) / d[a];
+            if (t > ta && t < tb) tbuf[m++] = t;
+        }
+    }
+    qsort(tbuf, (size_t)m, sizeof(double), cmp_double);
+    int cnt = 0;
+    for (int i = 0; i + 1 < m; ++i) {
+        double t0 = tbuf[i], t1 = tbuf[i + 1];
+        if (!(t1 > t0)) continue;
+        double tm = 0.5 * (t0 + t1);
+        int64_t idx[3];
+        for (int a = 0; a < 3; ++a) {
+            double c = floor((p[a] + tm * d[a] - s->origin[a]) / s->voxel);
+            if (c < 0) c = 0;
+            if (c > n[a] - 1) c = n[a] - 1;
+            idx[a] = (int64_t)c;
+        }
+        out[cnt].v = idx[0] + (int64_t)s->nx * (idx[1] + (int64_t)s->ny * idx[2]);
+        out[cnt].t0 = t0;
+        out[cnt].t1 = t1;
+        ++cnt;
+    }
+    return cnt;
+}
+
+static int max_intervals(const or_scene* s) { return s->nx + s->ny + s->nz + 8; }
+
+static double beta_tot(const or_scene* s, const float* bc, int64_t v) { return (double)bc[v] + s->beta_air; }
+
+/* sum of beta * length over the intervals (optical depth) */
+static double optical_depth(const or_scene* s, const float* bc, const ivl* iv, int n)
+{
+    double tau = 0.0;
+    for (int i = 0; i < n; ++i) tau += beta_tot(s, bc, iv[i].v) * (iv[i].t1 - iv[i].t0);
+    return tau;
+}
+
+/* exported: transmittance exp(-tau) between p and p + tmax d (d unit) */
+double or_transmittance(const or_scene* s, const float* bc, const double p[3], const double d[3], double tmax)
+{
+    ivl* iv = (ivl*)malloc(sizeof(ivl) * (size_t)max_intervals(s));
+    double* tb = (double*)malloc(sizeof(double) * (size_t)max_intervals(s));
+    int n = intervals(s, p, d, tmax, iv, tb);
+    double tau = optical_depth(s, bc, iv, n);
+    free(iv); free(tb);
+    return exp(-tau);
+}
+
+/* exported: voxel intervals, for the geometry pins */
+int or_intervals(const or_scene* s, const double p[3], const double d[3], double tmax,
+                 int64_t* vox, double* len, int cap)
+{
+    ivl* iv = (ivl*)malloc(sizeof(ivl) * (size_t)max_intervals(s));
+    double* tb = (double*)malloc(sizeof(double) * (size_t)max_intervals(s));
+    int n = intervals(s, p, d, tmax, iv, tb);
+    if (n > cap) n = cap;
+    for (int i = 0; i < n; ++i) { vox[i] = iv[i].v; len[i] = iv[i].t1 - iv[i].t0; }
+    free(iv); free(tb);
+    return n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* cameras: pinhole, image plane at unit distance along the forward axis.   */
+/* READING (pixel response W_d is not given for a perspective pixel): a     */
+/* point whose projection falls in pixel d has W_d = 1 / Omega_d, Omega_d    */
+/* being the pixel's exact solid angle, so the pixel value is the radiance  */
+/* averaged over its solid angle; pixel (col,row) = floor of the scaled     */
+/* image-plane coordinates, row 0 at the top, edges go to the higher index. */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double C[3], F[3], R[3], U[3];
+    double tx, ty;
+    int W, H;
+    int64_t off;   /* offset of the camera's first pixel in the image array */
+} ocam;
+
+static void setup_cams(const or_scene* s, ocam* cams)
+{
+    int64_t off = 0;
+    for (int c = 0; c < s->n_cams; ++c) {
+        const double* q = s->cams + 12 * c;
+        ocam* k = &cams[c];
+        for (int i = 0; i < 3; ++i) { k->C[i] = q[i]; k->F[i] = q[3 + i] - q[i]; }
+        normalize3(k->F);
+        cross3(k->F, q + 6, k->R);
+        normalize3(k->R);
+        cross3(k->R, k->F, k->U);
+        k->W = (int)q[10];
+        k->H = (int)q[11];
+        k->ty = tan(0.5 * q[9]);
+        k->tx = k->ty * (double)k->W / (double)k->H;
+        k->off = off;
+        off += (int64_t)k->W * k->H;
+    }
+}
+
+/* solid angle of [0,x] x [0,y] on the plane at unit distance (signed) */
+static double rect_sa(double x, double y) { return atan(x * y / sqrt(1.0 + x * x + y * y)); }
+
+double or_pixel_solid_angle(double tx, double ty, int W, int H, int col, int row)
+{
+    double xa = tx * (-1.0 + 2.0 * col / (double)W), xb = tx * (-1.0 + 2.0 * (col + 1) / (double)W);
+    double ya = ty * (1.0 - 2.0 * (row + 1) / (double)H), yb = ty * (1.0 - 2.0 * row / (double)H);
+    return rect_sa(xb, yb) - rect_sa(xa, yb) - rect_sa(xb, ya) + rect_sa(xa, ya);
+}
+
+/* pixel of point x in camera k, -1 if behind or outside the image */
+static int64_t project(const ocam* k, const double x[3], int* col_out, int* row_out)
+{
+    double q[3] = {x[0] - k->C[0], x[1] - k->C[1], x[2] - k->C[2]};
+    double z = dot3(q, k->F);
+    if (!(z > 0.0)) return -1;
+    double sx = dot3(q, k->R) / (z * k->tx);
+    double sy = dot3(q, k->U) / (z * k->ty);
+    double fc = floor((sx + 1.0) * 0.5 * k->W);
+    double fr = floor((1.0 - sy) * 0.5 * k->H);
+    if (fc < 0 || fc >= k->W || fr < 0 || fr >= k->H) return -1;
+    *col_out = (int)fc;
+    *row_out = (int)fr;
+    return (int64_t)fr * k->W + (int64_t)fc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* medium (Sec. 4.4): beta = beta_c + beta_a, scattering function            */
+/* f_s = beta_s^c f^c + beta_s^a f^a = albedo_c beta_c f^c + albedo_a        */
+/* beta_a f^a (Eq. fs_scattering), albedo = beta_s / beta (Eq. eff_sinscat) */
+/* ------------------------------------------------------------------------ */
+static double fs_medium(const or_scene* s, double bc, double mu)
+{
+    return s->albedo_cloud * bc * or_phase_hg(s->hg_g, mu) + s->albedo_air * s->beta_air * or_phase_rayleigh(mu);
+}
+static double beta_s(const or_scene* s, double bc) { return s->albedo_cloud * bc + s->albedo_air * s->beta_air; }
+
+/* ------------------------------------------------------------------------ */
+/* sun source.  READING (the derivation uses an isotropic point light, the  */
+/* experiments a sun with parallel rays): start points are uniform on the   */
+/* rectangle normal to the sun direction that bounds the projected box;     */
+/* the first ray runs along the sun direction; the emitted-radiance over    */
+/* start-pdf factor is F0 * A (A = rectangle area); rays that miss the box  */
+/* count in N and contribute nothing.                                       */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double e1[3], e2[3];
+    double amin, amax, bmin, bmax, hmin;
+    double area;
+} osun;
+
+static void setup_sun(const or_scene* s, osun* o)
+{
+    or_onb(s->sun, o->e1, o->e2);
+    double L[3] = {s->nx * s->voxel, s->ny * s->voxel, s->nz * s->voxel};
+    o->amin = o->bmin = o->hmin = INFINITY;
+    o->amax = o->bmax = -INFINITY;
+    for (int c = 0; c < 8; ++c) {
+        double p[3];
+        for (int a = 0; a < 3; ++a) p[a] = s->origin[a] + ((c >> a) & 1) * L[a];
+        double pa = dot3(p, o->e1), pb = dot3(p, o->e2), ph = dot3(p, s->sun);
+        o->amin = fmin(o->amin, pa); o->amax = fmax(o->amax, pa);
+        o->bmin = fmin(o->bmin, pb); o->bmax = fmax(o->bmax, pb);
+        o->hmin = fmin(o->hmin, ph);
+    }
+    o->hmin -= 1.0;
+    o->area = (o->amax - o->amin) * (o->bmax - o->bmin);
+}
+
+/* ------------------------------------------------------------------------ */
+/* one sampled path (Sec. 3.4): vertices x_0 (box entry) .. x_B (last       */
+/* collision), outgoing directions om_k, flight lengths l_k into x_k,       */
+/* collision voxels v_k.                                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int B, end, entered;
+    double x[OR_MAXV][3];
+    double om[OR_MAXV][3];
+    double l[OR_MAXV];
+    int64_t v[OR_MAXV];
+    int type[OR_MAXV];       /* particle type chosen at x_k: 0 cloud, 1 air, 2 none */
+} opath;
+
+typedef struct {
+    const or_scene* s;
+    osun sun;
+    ocam* cams;
+    ivl* iv;
+    double* tb;
+    ivl* iv2;
+    double* tb2;
+} octx;
+
+/*
+ * Sample path `pid` under extinction bc (Secs. 3.4.1-3.4.2).
+ *  - distance: tau ~ Exp(1), the flight ends where the optical depth from
+ *    the previous vertex reaches tau (collision), or at the box exit (escape);
+ *    a collision needs beta > 0 in its voxel;
+ *  - READING (Sec. 3.4.2 picks the type by extinction, while Appendix B
+ *    needs the direction pdf to be f_p, which weights types by their
+ *    scattering coefficient): the type is picked with probability
+ *    albedo_j beta_j / beta_s, which makes the direction pdf exactly f_p;
+ *  - READING (termination; the paper ends only on escape): after the local
+ *    estimates at collision k, the path stops if k == max_orders, and for
+ *    k >= rr_start it survives with constant probability q, its weight
+ *    divided by q.  A constant q does not depend on the medium and cancels
+ *    in the recycling ratio.
+ * Tallies follow the physical weight for the energy-balance check.
+ */
+static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double* tal)
+{
+    const or_scene* s = c->s;
+    double u[4];
+    double w0 = s->sun_irradiance * c->sun.area;
+    draw(s, pid, 0, 0, u);
+    double a = c->sun.amin + u[0] * (c->sun.amax - c->sun.amin);
+    double b = c->sun.bmin + u[1] * (c->sun.bmax - c->sun.bmin);
+    double p[3];
+    for (int i = 0; i < 3; ++i) p[i] = a * c->sun.e1[i] + b * c->sun.e2[i] + c->sun.hmin * s->sun[i];
+    double ta, tbx;
+    P->B = 0;
+    P->end = END_NONE;
+    if (!clip_box(s, p, s->sun, INFINITY, &ta, &tbx)) {
+        P->entered = 0;
+        P->end = END_MISS;
+        if (tal) tal[T_MISSED] += w0;
+        return;
+    }
+    P->entered = 1;
+    if (tal) { tal[T_INJECTED] += w0; tal[T_ENTERED] += 1.0; }
+    for (int i = 0; i < 3; ++i) { P->x[0][i] = p[i] + ta * s->sun[i]; P->om[0][i] = s->sun[i]; }
+    P->v[0] = -1;
+    P->l[0] = 0.0;
+    P->type[0] = 2;
+    double w = w0;
+    double tau = -log(u[2]);
+    for (int k = 1;; ++k) {
+        /* distance sampling from x_{k-1} along om_{k-1} */
+        int n = intervals(s, P->x[k - 1], P->om[k - 1], INFINITY, c->iv, c->tb);
+        double acc = 0.0;
+        int hit = 0;
+        double tcol = 0.0;
+        int64_t vcol = -1;
+        for (int i = 0; i < n; ++i) {
+            double bt = beta_tot(s, bc, c->iv[i].v);
+            double len = c->iv[i].t1 - c->iv[i].t0;
+            if (tal) tal[T_SEG_CROSS] += 1.0;
+            if (bt > 0.0 && tau - acc <= bt * len) {
+                tcol = c->iv[i].t0 + (tau - acc) / bt;
+                vcol = c->iv[i].v;
+                hit = 1;
+                break;
+            }
+            acc += bt * len;
+        }
+        if (!hit) {
+            P->end = END_ESCAPE;
+            if (tal) tal[T_ESCAPED] += w;
+            return;
+        }
+        for (int i = 0; i < 3; ++i) P->x[k][i] = P->x[k - 1][i] + tcol * P->om[k - 1][i];
+        P->l[k] = tcol;
+        P->v[k] = vcol;
+        P->type[k] = 2;
+        P->B = k;
+        double bcv = (double)bc[vcol];
+        double alb = beta_s(s, bcv) / beta_tot(s, bc, vcol);
+        if (tal) { tal[T_COLLISIONS] += 1.0; tal[T_ABSORBED] += w * (1.0 - alb); }
+        w *= alb;
+        draw(s, pid, (uint32_t)k, 0, u);
+        if (k == s->max_orders) {
+            P->end = END_TRUNC;
+            if (tal) tal[T_TRUNCATED] += w;
+            return;
+        }
+        if (k >= s->rr_start) {
+            if (u[0] <= s->rr_q) {
+                if (tal) tal[T_RR_GAIN] += w * (1.0 / s->rr_q - 1.0);
+                w /= s->rr_q;
+            } else {
+                P->end = END_RR;
+                if (tal) tal[T_RR_KILLED] += w;
+                return;
+            }
+        }
+        /* particle type, then direction from that type's phase function */
+        double bsc = s->albedo_cloud * bcv;
+        int cloud = (u[1] * beta_s(s, bcv) <= bsc);
+        P->type[k] = cloud ? 0 : 1;
+        double mu = cloud ? or_sample_hg(s->hg_g, u[2]) : or_sample_rayleigh(u[2]);
+        or_rotate(P->om[k - 1], mu, 2.0 * OR_PI * u[3], P->om[k]);
+        draw(s, pid, (uint32_t)k, 1, u);
+        tau = -log(u[0]);
+        if (k + 1 >= OR_MAXV) { P->end = END_TRUNC; return; }
+    }
+}
+
+/*
+ * Evaluate the sampled path under extinction bt (paths drawn under br):
+ * every event b = 1..B is a local estimate toward each camera (Eq. Qd);
+ * its estimate of f(x|M_t)/mu(x|M_ref) (Eq. forward_simualtion_recycling)
+ * is written out factor by factor:
+ *   F0 A                                  source radiance / start pdf
+ *   prod_{k<=b} T_t(seg k)/T_ref(seg k)   flights x_{k-1} -> x_k; the
+ *                                         beta(x_k) factor of the distance pdf
+ *                                         is kept with the vertex below
+ *   prod_{k<b} f_s,t(x_k, mu_k) / (beta_ref(x_k) f_p,ref(x_k, mu_k))
+ *                                         scattering vs. collision and
+ *                                         direction pdfs (Eqs. gk_scatter,
+ *                                         final_mu)
+ *   f_s,t(x_b, mu_bd) / beta_ref(x_b)     local estimate (P_le of Sec. 3.4.3)
+ *   T_t(x_b -> C_d) / |x_b - C_d|^2       shadow ray and G
+ *   1 / Omega_d                           pixel response
+ *   q^-(number of roulette survivals)     termination pdf
+ * READING (Eq. Qd's indices are garbled): event b uses the albedo-like
+ * factors of vertices 1..b, the phase function at x_b for the angle between
+ * om_{b-1} and the direction to the camera, and the transmittance from x_b
+ * to the camera.
+ * READING (the correction factor of Eq. 20 is written for a whole path):
+ * each event is its own sub-path, so its ratio covers vertices 0..b.
+ *
+ * With dldi != NULL the loss gradient is accumulated: for each event,
+ * a = dL/dI[pixel] * contribution, times the path score function of
+ * Sec. 4.4 written for the sub-path ending at the camera:
+ *   -sum_{k=1..b} l_{k,v}  - l_{(b->d),v}
+ *   + sum_{k=1..b-1} [x_k in v] h(x_k, mu_k) + [x_b in v] h(x_b, mu_bd),
+ *   h = albedo_c f^c(mu) / f_s,t(mu)   (Eq. fs_deriv).
+ * READING (the paper's sums run over vertex 0, the source, which has no
+ * scattering term, and over the segment after the last vertex): vertex
+ * terms cover the scattering vertices of the sub-path only, segment terms
+ * its sampled flights plus the shadow ray; the escape flight is in no
+ * sub-path.  Events with zero contribution are skipped (their score may be
+ * infinite where beta_c = 0 and there is no air).
+ */
+static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
+                      double inv_norm, double* img, const double* dldi,
+                      double* grad, double* gabs, double* tal, uint64_t* fp)
+{
+    const or_scene* s = c->s;
+    uint64_t h = 0xcbf29ce484222325ull;
+    h = fnv_word(h, (uint32_t)P->B);
+    h = fnv_word(h, (uint32_t)P->end);
+    if (!P->entered) { if (fp) *fp = h; return; }
+    double w0 = s->sun_irradiance * c->sun.area;
+    double log_tr = 0.0;       /* sum over flights of tau_ref - tau_t */
+    double vert = 1.0;         /* product of the vertex ratios k < b  */
+    for (int b = 1; b <= P->B; ++b) {
+        int n = intervals(s, P->x[b - 1], P->om[b - 1], P->l[b], c->iv, c->tb);
+        log_tr += optical_depth(s, br, c->iv, n) - optical_depth(s, bt, c->iv, n);
+        if (b >= 2) {
+            int64_t vk = P->v[b - 1];
+            double mu = dot3(P->om[b - 2], P->om[b - 1]);
+            double bref = (double)br[vk];
+            double fs_ref = fs_medium(s, bref, mu);
+            if (fs_ref == 0.0) {
+                vert = 0.0;       /* zero weight under M_ref from here on */
+            } else {
+                double fp_ref = fs_ref / beta_s(s, bref);
+                vert *= fs_medium(s, (double)bt[vk], mu) / (beta_tot(s, br, vk) * fp_ref);
+            }
+        }
+        int nrr = b - s->rr_start;
+        if (nrr < 0) nrr = 0;
+        double base = w0 * exp(log_tr) * vert * pow(s->rr_q, -(double)nrr);
+        int64_t vb = P->v[b];
+        h = fnv_word(h, (uint32_t)vb);
+        h = fnv_word(h, (uint32_t)P->type[b]);
+        for (int d = 0; d < s->n_cams; ++d) {
+            const ocam* k = &c->cams[d];
+            int col, row;
+            int64_t pix = project(k, P->x[b], &col, &row);
+            h = fnv_word(h, (uint32_t)(int32_t)pix);
+            if (pix < 0) continue;
+            double to[3] = {k->C[0] - P->x[b][0], k->C[1] - P->x[b][1], k->C[2] - P->x[b][2]};
+            double r2 = dot3(to, to);
+            double r = sqrt(r2);
+            double dir[3] = {to[0] / r, to[1] / r, to[2] / r};
+            double mu = dot3(P->om[b - 1], dir);
+            int ns = intervals(s, P->x[b], dir, r, c->iv2, c->tb2);
+            double T = exp(-optical_depth(s, bt, c->iv2, ns));
+            double om = or_pixel_solid_angle(k->tx, k->ty, k->W, k->H, col, row);
+            double ev = base * fs_medium(s, (double)bt[vb], mu) / beta_tot(s, br, vb) * T / r2 / om;
+            if (tal) { tal[T_IN_VIEW] += 1.0; tal[T_SHADOW_CROSS] += (double)ns; }
+            int64_t gp = k->off + pix;
+            if (img) img[gp] += ev * inv_norm;
+            if (!dldi || ev == 0.0) continue;
+            double A = dldi[gp] * ev * inv_norm;
+            /* flights 1..b */
+            for (int j = 1; j <= b; ++j) {
+                int nj = intervals(s, P->x[j - 1], P->om[j - 1], P->l[j], c->iv, c->tb);
+                for (int i = 0; i < nj; ++i) {
+                    double t = A * (c->iv[i].t1 - c->iv[i].t0);
+                    grad[c->iv[i].v] -= t;
+                    if (gabs) gabs[c->iv[i].v] += fabs(t);
+                }
+            }
+            /* shadow ray x_b -> camera */
+            for (int i = 0; i < ns; ++i) {
+                double t = A * (c->iv2[i].t1 - c->iv2[i].t0);
+                grad[c->iv2[i].v] -= t;
+                if (gabs) gabs[c->iv2[i].v] += fabs(t);
+            }
+            /* scattering vertices 1..b-1 (angle between sampled directions) */
+            for (int j = 1; j < b; ++j) {
+                int64_t vj = P->v[j];
+                double muj = dot3(P->om[j - 1], P->om[j]);
+                double t = A * s->albedo_cloud * or_phase_hg(s->hg_g, muj) / fs_medium(s, (double)bt[vj], muj);
+                grad[vj] += t;
+                if (gabs) gabs[vj] += fabs(t);
+            }
+            /* vertex b toward the camera */
+            {
+                double t = A * s->albedo_cloud * or_phase_hg(s->hg_g, mu) / fs_medium(s, (double)bt[vb], mu);
+                grad[vb] += t;
+                if (gabs) gabs[vb] += fabs(t);
+            }
+        }
+    }
+    if (fp) *fp = h;
+}
+
+static int64_t total_pixels(const or_scene* s)
+{
+    int64_t n = 0;
+    for (int c = 0; c < s->n_cams; ++c) n += (int64_t)s->cams[12 * c + 10] * (int64_t)s->cams[12 * c + 11];
+    return n;
+}
+
+/*
+ * Paths first_path .. first_path+n_paths-1, sampled under beta_ref and
+ * evaluated under beta_t (pass the same grid for plain path tracing).
+ * images (sum of camera W*H, camera-major, row-major) receive the event
+ * contributions divided by n_norm; grad/gabs (V doubles) receive the loss
+ * gradient and the sum of the absolute values of its terms when dldi is
+ * given.  All outputs are accumulated into; tallies (T_COUNT doubles) and
+ * fingerprints (n_paths) are optional.  threads > 1 splits paths over
+ * OpenMP threads with private buffers (summation order then differs).
+ */
+int or_render(const or_scene* s, const float* beta_ref, const float* beta_t,
+              uint64_t first_path, uint64_t n_paths, double n_norm,
+              double* images, const double* dldi, double* grad, double* gabs,
+              double* tallies, uint64_t* fingerprints, int threads)
+{
+    if (s->max_orders + 1 >= OR_MAXV || s->max_orders < 1) return -1;
+    int64_t npix = total_pixels(s);
+    int64_t nvox = (int64_t)s->nx * s->ny * s->nz;
+    double inv_norm = 1.0 / n_norm;
+    if (threads < 1) threads = 1;
+#ifndef _OPENMP
+    threads = 1;
+#endif
+    int err = 0;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(threads)
+#endif
+    {
+        int tid = 0, nt = 1;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+        nt = omp_get_num_threads();
+#endif
+        octx c;
+        c.s = s;
+        setup_sun(s, &c.sun);
+        c.cams = (ocam*)malloc(sizeof(ocam) * (size_t)(s->n_cams > 0 ? s->n_cams : 1));
+        setup_cams(s, c.cams);
+        int mi = max_intervals(s);
+        c.iv = (ivl*)malloc(sizeof(ivl) * (size_t)mi);
+        c.tb = (double*)malloc(sizeof(double) * (size_t)mi);
+        c.iv2 = (ivl*)malloc(sizeof(ivl) * (size_t)mi);
+        c.tb2 = (double*)malloc(sizeof(double) * (size_t)mi);
+        opath* P = (opath*)malloc(sizeof(opath));
+        double* img = images;
+        double* g = grad;
+        double* ga = gabs;
+        double tal[T_COUNT];
+        memset(tal, 0, sizeof(tal));
+        if (nt > 1) {
+            img = images ? (double*)calloc((size_t)npix, sizeof(double)) : NULL;
+            g = grad ? (double*)calloc((size_t)nvox, sizeof(double)) : NULL;
+            ga = gabs ? (double*)calloc((size_t)nvox, sizeof(double)) : NULL;
+        }
+        for (uint64_t i = (uint64_t)tid; i < n_paths; i += (uint64_t)nt) {
+            uint64_t pid = first_path + i;
+            sample_path(&c, beta_ref, pid, P, tal);
+            eval_path(&c, beta_ref, beta_t, P, inv_norm, img, dldi, g, ga, tal,
+                      fingerprints ? &fingerprints[i] : NULL);
+        }
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+        {
+            if (nt > 1) {
+                if (img) for (int64_t j = 0; j < npix; ++j) images[j] += img[j];
+                if (g) for (int64_t j = 0; j < nvox; ++j) grad[j] += g[j];
+                if (ga) for (int64_t j = 0; j < nvox; ++j) gabs[j] += ga[j];
+            }
+            if (tallies) for (int j = 0; j < T_COUNT; ++j) tallies[j] += tal[j];
+        }
+        if (nt > 1) { free(img); free(g); free(ga); }
+        free(P); free(c.iv); free(c.tb); free(c.iv2); free(c.tb2); free(c.cams);
+    }
+    return err;
+}
+
+/* Vertices of one path, for inspection: returns B; x (3*(B+1)), om, v, l */
+int or_path(const or_scene* s, const float* beta, uint64_t pid, double* x, double* om, int64_t* v, double* l, int* end)
+{
+    octx c;
+    c.s = s;
+    setup_sun(s, &c.sun);
+    int mi = max_intervals(s);
+    c.cams = NULL;
+    c.iv = (ivl*)malloc(sizeof(ivl) * (size_t)mi);
+    c.tb = (double*)malloc(sizeof(double) * (size_t)mi);
+    opath* P = (opath*)malloc(sizeof(opath));
+    sample_path(&c, beta, pid, P, NULL);
+    int B = P->entered ? P->B : -1;
+    for (int k = 0; k <= P->B && P->entered; ++k) {
+        for (int i = 0; i < 3; ++i) { x[3 * k + i] = P->x[k][i]; om[3 * k + i] = P->om[k][i]; }
+        v[k] = P->v[k];
+        l[k] = P->l[k];
+    }
+    *end = P->end;
+    free(P); free(c.iv); free(c.tb);
+    return B;
+}
+
+/* sun rectangle (for the host-side checks): e1, e2, amin, amax, bmin, bmax, hmin, area */
+void or_sun_rect(const or_scene* s, double* out)
+{
+    osun o;
+    setup_sun(s, &o);
+    for (int i = 0; i < 3; ++i) { out[i] = o.e1[i]; out[3 + i] = o.e2[i]; }
+    out[6] = o.amin; out[7] = o.amax; out[8] = o.bmin; out[9] = o.bmax; out[10] = o.hmin; out[11] = o.area;
+}
+
+/*
+ * Deterministic single-scattering image by quadrature (a pin for first-order
+ * Monte-Carlo): per pixel, sub x sub stratified rays through the pixel,
+ * weighted by their solid angle; along each ray the in-scattered radiance
+ * beta_s f_p F0 T_sun(x) T_view(x) (first-order term of the integrated RTE,
+ * Sec. 3.2) is integrated with `steps` midpoint steps per voxel interval.
+ */
+void or_single_scatter_quad(const or_scene* s, const float* bc, int sub, int steps, double* images)
+{
+    int mi = max_intervals(s);
+    ocam* cams = (ocam*)malloc(sizeof(ocam) * (size_t)s->n_cams);
+    setup_cams(s, cams);
+    double ms[3] = {-s->sun[0], -s->sun[1], -s->sun[2]};
+    for (int cidx = 0; cidx < s->n_cams; ++cidx) {
+        const ocam* k = &cams[cidx];
+        int64_t npx = (int64_t)k->W * k->H;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic)
+#endif
+        for (int64_t pix = 0; pix < npx; ++pix) {
+            ivl* iv = (ivl*)malloc(sizeof(ivl) * (size_t)mi);
+            double* tb = (double*)malloc(sizeof(double) * (size_t)mi);
+            ivl* iv2 = (ivl*)malloc(sizeof(ivl) * (size_t)mi);
+            double* tb2 = (double*)malloc(sizeof(double) * (size_t)mi);
+            int col = (int)(pix % k->W), row = (int)(pix / k->W);
+            double num = 0.0, den = 0.0;
+            for (int i = 0; i < sub; ++i) {
+                for (int j = 0; j < sub; ++j) {
+                    double sx = -1.0 + 2.0 * (col + (i + 0.5) / sub) / k->W;
+                    double sy = 1.0 - 2.0 * (row + (j + 0.5) / sub) / k->H;
+                    double x = sx * k->tx, y = sy * k->ty;
+                    double wgt = 1.0 / pow(1.0 + x * x + y * y, 1.5);
+                    double d[3];
+                    for (int a = 0; a < 3; ++a) d[a] = k->F[a] + x * k->R[a] + y * k->U[a];
+                    normalize3(d);
+                    double mu = -dot3(s->sun, d);   /* sun direction vs. toward-camera direction */
+                    int n = intervals(s, k->C, d, INFINITY, iv, tb);
+                    double Tv = 1.0, L = 0.0;
+                    for (int q = 0; q < n; ++q) {
+                        double bcv = (double)bc[iv[q].v];
+                        double bt = bcv + s->beta_air;
+                        double fsv = fs_medium(s, bcv, mu);
+                        double h = (iv[q].t1 - iv[q].t0) / steps;
+                        for (int m = 0; m < steps; ++m) {
+                            double t = iv[q].t0 + (m + 0.5) * h;
+                            double p[3];
+                            for (int a = 0; a < 3; ++a) p[a] = k->C[a] + t * d[a];
+                            int n2 = intervals(s, p, ms, INFINITY, iv2, tb2);
+                            double Ts = exp(-optical_depth(s, bc, iv2, n2));
+                            double Tw = Tv * exp(-bt * (m + 0.5) * h);
+                            L += fsv * s->sun_irradiance * Ts * Tw * h;
+                        }
+                        Tv *= exp(-bt * (iv[q].t1 - iv[q].t0));
+                    }
+                    num += wgt * L;
+                    den += wgt;
+                }
+            }
+            images[k->off + pix] = num / den;
+            free(iv); free(tb); free(iv2); free(tb2);
+        }
+    }
+    free(cams);
+}
+
+/* exported geometry of a camera (C, F, R, U, tx, ty), for the host checks */
+void or_camera_frame(const or_scene* s, int cam, double* out)
+{
+    ocam* cams = (ocam*)malloc(sizeof(ocam) * (size_t)s->n_cams);
+    setup_cams(s, cams);
+    const ocam* k = &cams[cam];
+    for (int i = 0; i < 3; ++i) { out[i] = k->C[i]; out[3 + i] = k->F[i]; out[6 + i] = k->R[i]; out[9 + i] = k->U[i]; }
+    out[12] = k->tx; out[13] = k->ty;
+    free(cams);
+}
+
+int or_tally_count(void) { return T_COUNT; }

@@ -1,0 +1,413 @@
+"""Pins of the FP64 CPU oracle against facts the paper and mathematics fix.
+
+Nothing here compares the oracle with itself or with the CUDA path: every
+check is a published known answer, a closed form, an invariant, a special
+case or brute force.  Each test names the part of the oracle it pins.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle as O
+from paper_2110_00085_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Philox ---
+def test_philox_known_answers():
+    """Random123 known-answer vectors for Philox4x32-10 (Salmon et al. SC'11)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = O.philox(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_fnv_offset_basis():
+    """FNV-1a 64 of the empty input is the published offset basis."""
+    assert O.fnv1a_words([]) == 0xCBF29CE484222325
+
+
+# --------------------------------------------------------- phase functions --
+@pytest.mark.parametrize("g", [0.0, 0.5, 0.85, -0.3])
+def test_hg_normalised_and_mean_cosine(g):
+    """HG integrates to 1 over the sphere (Eq. phase_conservation) and its
+    mean cosine equals its asymmetry parameter g."""
+    norm = 2 * math.pi * integrate.quad(lambda m: O.phase_hg(g, m), -1, 1, limit=200, epsabs=1e-13)[0]
+    mean = 2 * math.pi * integrate.quad(lambda m: m * O.phase_hg(g, m), -1, 1, limit=200, epsabs=1e-13)[0]
+    assert abs(norm - 1) < 1e-9
+    assert abs(mean - g) < 1e-9
+
+
+def test_hg_isotropic_special_case():
+    for mu in (-1, -0.3, 0, 0.7, 1):
+        assert abs(O.phase_hg(0.0, mu) - 1 / (4 * math.pi)) < 1e-15
+
+
+def test_rayleigh_moments():
+    """Rayleigh: normalised, mean cosine 0, <mu^2> = 2/5."""
+    f = O.phase_rayleigh
+    n = 2 * math.pi * integrate.quad(f, -1, 1)[0]
+    m1 = 2 * math.pi * integrate.quad(lambda m: m * f(m), -1, 1)[0]
+    m2 = 2 * math.pi * integrate.quad(lambda m: m * m * f(m), -1, 1)[0]
+    assert abs(n - 1) < 1e-12 and abs(m1) < 1e-12 and abs(m2 - 0.4) < 1e-12
+
+
+@pytest.mark.parametrize("g", [0.85, 0.5, -0.4])
+def test_hg_sampler_inverts_cdf(g):
+    """The HG sampler is the inverse of the closed-form HG CDF in mu."""
+    def cdf(mu):
+        return (1 - g * g) / (2 * g) * (1 / math.sqrt(1 + g * g - 2 * g * mu) - 1 / (1 + g))
+    for u in np.linspace(1e-6, 1, 101):
+        assert abs(cdf(O.sample_hg(g, u)) - u) < 1e-9
+
+
+def test_rayleigh_sampler_inverts_cdf():
+    """Rayleigh CDF in mu is (mu^3 + 3 mu + 4)/8; the sampler inverts it."""
+    for u in np.linspace(1e-6, 1, 101):
+        mu = O.sample_rayleigh(u)
+        assert abs((mu ** 3 + 3 * mu + 4) / 8 - u) < 1e-12
+
+
+def test_sampler_cdf_matches_pdf_integral():
+    """The sampled distribution's CDF equals the integral of the pdf the
+    estimator divides by (ties the sampler to the evaluated phase)."""
+    g = 0.85
+    for u in (0.1, 0.5, 0.9, 0.99):
+        mu = O.sample_hg(g, u)
+        F = 2 * math.pi * integrate.quad(lambda m: O.phase_hg(g, m), -1, mu, limit=200, epsabs=1e-13)[0]
+        assert abs(F - u) < 1e-8
+        mu = O.sample_rayleigh(u)
+        F = 2 * math.pi * integrate.quad(O.phase_rayleigh, -1, mu)[0]
+        assert abs(F - u) < 1e-12
+
+
+# ------------------------------------------------------ directions, bases --
+def test_onb_orthonormal_right_handed():
+    rng = np.random.default_rng(0)
+    ns = [np.array(v, float) for v in [(0, 0, 1), (0, 0, -1), (1, 0, 0), (0, 1, 0)]]
+    ns += [v / np.linalg.norm(v) for v in rng.normal(size=(50, 3))]
+    for n in ns:
+        b1, b2 = O.onb(n)
+        M = np.stack([b1, b2, n])
+        assert np.allclose(M @ M.T, np.eye(3), atol=1e-12)
+        assert np.allclose(np.cross(b1, b2), n, atol=1e-12)
+
+
+def test_rotation_sets_polar_and_azimuth():
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        d = rng.normal(size=3); d /= np.linalg.norm(d)
+        mu = rng.uniform(-1, 1); phi = rng.uniform(0, 2 * math.pi)
+        o = O.rotate(d, mu, phi)
+        b1, b2 = O.onb(d)
+        st = math.sqrt(1 - mu * mu)
+        assert abs(np.linalg.norm(o) - 1) < 1e-12
+        assert abs(o @ d - mu) < 1e-12
+        assert abs(o @ b1 - st * math.cos(phi)) < 1e-12
+        assert abs(o @ b2 - st * math.sin(phi)) < 1e-12
+
+
+# ------------------------------------------------------------- cameras ------
+def test_pixel_solid_angles_tile_the_image():
+    """Pixel solid angles add up to the image rectangle's solid angle, and the
+    whole plane (tan -> inf) is a hemisphere, 2 pi."""
+    tx, ty, W, H = 0.6, 0.45, 24, 18
+    tot = sum(O.pixel_solid_angle(tx, ty, W, H, c, r) for c in range(W) for r in range(H))
+    full = 4 * math.atan(tx * ty / math.sqrt(1 + tx * tx + ty * ty))
+    assert abs(tot - full) < 1e-12
+    assert abs(O.pixel_solid_angle(1e9, 1e9, 1, 1, 0, 0) - 2 * math.pi) < 1e-6
+
+
+def test_small_pixel_solid_angle_is_area_cos3():
+    """A tiny pixel at image-plane position (x, y) subtends area*cos^3."""
+    tx = ty = 0.5
+    W = H = 2001
+    for c, r in [(1000, 1000), (1800, 300), (50, 1950)]:
+        om = O.pixel_solid_angle(tx, ty, W, H, c, r)
+        x = tx * (-1 + 2 * (c + 0.5) / W)
+        y = ty * (1 - 2 * (r + 0.5) / H)
+        area = (2 * tx / W) * (2 * ty / H)
+        cos3 = (1 + x * x + y * y) ** -1.5
+        assert abs(om / (area * cos3) - 1) < 1e-5
+
+
+def test_camera_frame():
+    sc = synth.config(1, n_paths=16)
+    for i, cam in enumerate(sc.cameras):
+        f = O.camera_frame(sc, i)
+        fwd = np.subtract(cam.look_at, cam.pos); fwd /= np.linalg.norm(fwd)
+        assert np.allclose(f["F"], fwd)
+        assert abs(f["R"] @ f["F"]) < 1e-12 and abs(f["U"] @ f["F"]) < 1e-12
+        assert f["U"] @ np.array(cam.up) > 0
+        assert abs(f["ty"] - math.tan(cam.fov_y / 2)) < 1e-12
+
+
+# --------------------------------------------------- grid traversal (DDA) ---
+def _grid_scene(n=8, voxel=0.02):
+    return synth.Scene(name="g", n=(n, n, n), voxel=voxel, beta_cloud=np.zeros((n, n, n), np.float32))
+
+
+def test_intervals_axis_ray():
+    sc = _grid_scene()
+    d = 0.02
+    vox, ln = O.intervals(sc, (-0.1, 2.5 * d, 5.5 * d), (1, 0, 0), 10.0)
+    assert len(vox) == 8
+    assert np.allclose(ln, d)
+    assert list(vox) == [i + 8 * (2 + 8 * 5) for i in range(8)]
+
+
+def test_intervals_main_diagonal_through_corners():
+    """A ray through voxel corners: every interval is a full diagonal and
+    zero-length crossings are dropped."""
+    sc = _grid_scene()
+    d = 0.02
+    u = np.ones(3) / math.sqrt(3)
+    vox, ln = O.intervals(sc, -0.1 * u, u, 10.0)
+    assert len(vox) == 8
+    assert np.allclose(ln, math.sqrt(3) * d)
+    assert list(vox) == [i * (1 + 8 + 64) for i in range(8)]
+
+
+def test_optical_depth_matches_dense_sampling():
+    """Sum beta*l over intervals equals a dense midpoint integral of the
+    piecewise-constant field along random rays (brute force)."""
+    rng = np.random.default_rng(3)
+    n = 8
+    beta = rng.uniform(0, 30, size=(n, n, n)).astype(np.float32)
+    sc = synth.Scene(name="g", n=(n, n, n), voxel=0.02, beta_cloud=beta, beta_air=0.5)
+    L = n * 0.02
+    for _ in range(20):
+        p = rng.uniform(-0.05, L + 0.05, size=3)
+        d = rng.normal(size=3); d /= np.linalg.norm(d)
+        tmax = rng.uniform(0.05, 0.4)
+        tau = -math.log(O.transmittance(sc, beta, p, d, tmax))
+        m = 400000
+        t = (np.arange(m) + 0.5) * (tmax / m)
+        x = p[None, :] + t[:, None] * d[None, :]
+        inside = np.all((x >= 0) & (x < L), axis=1)
+        idx = np.floor(x[inside] / 0.02).astype(int)
+        b = beta[idx[:, 2], idx[:, 1], idx[:, 0]].astype(np.float64) + 0.5
+        ref = b.sum() * (tmax / m)
+        vox, ln = O.intervals(sc, p, d, tmax)
+        assert abs(ln.sum() - inside.sum() * tmax / m) < 3e-6
+        assert abs(tau - ref) <= 2e-5 * max(ref, 1.0)
+
+
+# ------------------------------------------------------------- sun source ---
+def test_sun_rectangle_hit_fraction():
+    """Start points are uniform on the sun rectangle: the fraction that
+    enters the box equals the box's projected area over the rectangle's
+    area (projected area of a box along s: sum over axes of the face
+    area times |s_axis|)."""
+    n = 16
+    sc = synth.Scene(name="s", n=(n, 8, 4), voxel=0.02,
+                     beta_cloud=np.zeros((4, 8, n), np.float32),
+                     sun_dir=synth.sun_from_zenith(40.0, 25.0), n_paths=1 << 16,
+                     cameras=synth.arc_cameras(1, (n * 0.02, 0.16, 0.08), 4, 4))
+    Lx, Ly, Lz = sc.box_size
+    s = np.abs(np.array(sc.sun_dir))
+    proj = Ly * Lz * s[0] + Lx * Lz * s[1] + Lx * Ly * s[2]
+    rect = O.sun_rect(sc)
+    p = proj / rect["area"]
+    r = O.render(sc, sc.beta_cloud, tallies=True)
+    frac = r["tallies"]["entered"] / sc.n_paths
+    sig = math.sqrt(p * (1 - p) / sc.n_paths)
+    assert abs(frac - p) < 4 * sig
+    w0 = rect["area"] * sc.sun_irradiance
+    assert abs(r["tallies"]["injected"] + r["tallies"]["missed"] - w0 * sc.n_paths) < 1e-9 * w0 * sc.n_paths
+
+
+# ------------------------------------------------------------ closed forms --
+def test_beer_lambert_pure_absorber():
+    """P-a: an absorbing cube (albedo 0) lit from the zenith: the escaping
+    weight fraction is exp(-beta L) (binomial 4 sigma); images are 0."""
+    n = 8
+    beta = np.full((n, n, n), 5.0, np.float32)
+    sc = synth.Scene(name="bl", n=(n, n, n), voxel=0.02, beta_cloud=beta, albedo_cloud=0.0,
+                     sun_dir=(0.0, 0.0, -1.0), n_paths=1 << 15,
+                     cameras=synth.arc_cameras(3, (0.16,) * 3, 8, 8))
+    r = O.render(sc, beta, tallies=True)
+    T = r["tallies"]
+    p = math.exp(-5.0 * 0.16)
+    frac = T["escaped"] / T["injected"]
+    sig = math.sqrt(p * (1 - p) / T["entered"])
+    assert abs(frac - p) < 4 * sig
+    assert np.all(r["images"] == 0.0)
+
+
+def _slab_scene(n_paths):
+    nxy, nz = 64, 2
+    beta = np.full((nz, nxy, nxy), 10.0, np.float32)
+    box = (nxy * 0.02, nxy * 0.02, nz * 0.02)
+    return synth.Scene(name="slab", n=(nxy, nxy, nz), voxel=0.02, beta_cloud=beta,
+                       albedo_cloud=0.99, hg_g=0.85, sun_dir=synth.sun_from_zenith(30.0),
+                       cameras=synth.arc_cameras(1, box, 16, 16), max_orders=1, rr_start=5,
+                       n_paths=n_paths)
+
+
+def test_homogeneous_slab_single_scattering():
+    """P-b: first-order radiance of a laterally infinite homogeneous slab,
+    L = w F0 p(Theta) mu0/(mu0+mu) [1 - exp(-tau*(1/mu0+1/mu))] (first-order
+    term of the integrated RTE of Sec. 3.2 for a collimated source); central
+    pixels of a wide thin slab, within 1% + 4 sigma."""
+    sc = _slab_scene(1 << 20)
+    r = O.render(sc, sc.beta_cloud, threads=8)
+    img = r["images"].reshape(16, 16)
+    f = O.camera_frame(sc, 0)
+    s = np.array(sc.sun_dir)
+    mu0 = -s[2]
+    tau = 10.0 * 0.04
+    vals, exp_ = [], []
+    for row in range(6, 10):
+        for col in range(6, 10):
+            x = f["tx"] * (-1 + 2 * (col + 0.5) / 16)
+            y = f["ty"] * (1 - 2 * (row + 0.5) / 16)
+            d = f["F"] + x * f["R"] + y * f["U"]
+            d /= np.linalg.norm(d)
+            mu = -d[2]
+            cth = -(s @ d)
+            Lx = 0.99 * sc.sun_irradiance * O.phase_hg(0.85, cth) * mu0 / (mu0 + mu) * (
+                1 - math.exp(-tau * (1 / mu0 + 1 / mu)))
+            vals.append(img[row, col]); exp_.append(Lx)
+    vals = np.array(vals); exp_ = np.array(exp_)
+    ratio = vals.sum() / exp_.sum()
+    assert abs(ratio - 1) < 0.01 + 4 * (np.std(vals / exp_) / math.sqrt(len(vals)))
+
+
+def _batch_images(sc, beta_ref, beta_t=None, blocks=16, seed=None, threads=8):
+    n = sc.n_paths // blocks
+    ims = []
+    for b in range(blocks):
+        r = O.render(sc, beta_ref, beta_t, first=b * n, n=n, threads=threads, seed=seed)
+        ims.append(r["images"])
+    ims = np.array(ims)
+    return ims.mean(0), ims.std(0, ddof=1) / math.sqrt(blocks)
+
+
+def test_single_scatter_quadrature_matches_first_order_mc():
+    """P-c: first-order Monte Carlo (max_orders = 1) equals a deterministic
+    quadrature of the first-order radiance on the same grid.  Pixels whose
+    quadrature is not converged (box edges) are excluded."""
+    sc = synth.small_scene(n=8, n_cams=2, px=12, peak=20.0, seed=11, n_paths=1 << 18)
+    sc = sc.replace(max_orders=1)
+    q_fine = O.single_scatter_quad(sc, sc.beta_cloud, sub=24, steps=8)
+    q_coarse = O.single_scatter_quad(sc, sc.beta_cloud, sub=12, steps=4)
+    mc, sd = _batch_images(sc, sc.beta_cloud)
+    use = q_fine > 0.05 * q_fine.max()
+    assert use.sum() >= 30
+    z = (mc[use] - q_fine[use]) / np.sqrt(sd[use] ** 2 + (q_fine[use] - q_coarse[use]) ** 2)
+    assert np.mean(z ** 2) < 2.5
+    assert np.max(np.abs(z)) < 5.0
+
+
+# --------------------------------------------------------------- invariants --
+def test_energy_balance_exact():
+    """P-d: injected + roulette gain = escaped + absorbed + truncated +
+    roulette-killed, per path, to FP64 rounding."""
+    for sc in (synth.config(1, n_paths=1 << 12), synth.config(2, n_paths=1 << 10)):
+        T = O.render(sc, sc.beta_cloud, tallies=True)["tallies"]
+        lhs = T["injected"] + T["rr_gain"]
+        rhs = T["escaped"] + T["absorbed"] + T["truncated"] + T["rr_killed"]
+        assert abs(lhs - rhs) < 1e-11 * lhs
+
+
+def test_conservative_medium_no_roulette():
+    """P-d at albedo 1 without roulette: what enters leaves (or is cut by the
+    order limit); nothing is absorbed."""
+    sc = synth.small_scene(n=8, n_cams=1, px=4, peak=5.0, seed=5, n_paths=1 << 12)
+    sc = sc.replace(albedo_cloud=1.0, max_orders=60, rr_start=100)
+    T = O.render(sc, sc.beta_cloud, tallies=True)["tallies"]
+    assert T["absorbed"] == 0.0 and T["rr_gain"] == 0.0
+    assert abs(T["escaped"] + T["truncated"] - T["injected"]) < 1e-11 * T["injected"]
+    assert T["truncated"] < 1e-3 * T["injected"]
+
+
+def test_recycling_ratio_is_one_at_reference():
+    """P-e (exact part): paths reused under the very extinction they were
+    drawn from reproduce the plain estimate bit for bit (r == 1)."""
+    sc = synth.small_scene(n=8, n_cams=3, px=8, seed=3, n_paths=1 << 10)
+    a = O.render(sc, sc.beta_cloud)["images"]
+    b = O.render(sc, sc.beta_cloud, sc.beta_cloud.copy())["images"]
+    assert np.array_equal(a, b)
+
+
+def test_recycled_estimator_unbiased():
+    """P-e: paths drawn under M_ref, reweighted to M_t, estimate the same
+    images as paths drawn under M_t (importance sampling is unbiased,
+    Appendix A) -- independent seeds, batch-means z-scores."""
+    sc = synth.small_scene(n=8, n_cams=3, px=6, seed=9, n_paths=1 << 16)
+    rng = np.random.default_rng(4)
+    bt = (sc.beta_cloud * rng.uniform(0.8, 1.3, size=sc.beta_cloud.shape)).astype(np.float32)
+    m1, s1 = _batch_images(sc, sc.beta_cloud, bt, seed=101)
+    m2, s2 = _batch_images(sc, bt, None, seed=202)
+    ok = (m1 + m2) > 1e-3 * (m1 + m2).max()
+    z = (m1[ok] - m2[ok]) / np.sqrt(s1[ok] ** 2 + s2[ok] ** 2)
+    assert np.mean(z ** 2) < 2.0
+    assert np.max(np.abs(z)) < 5.0
+    # camera totals (lower variance)
+    tot1, tot2 = m1.sum(), m2.sum()
+    assert abs(tot1 - tot2) < 4 * math.sqrt((s1 ** 2).sum() + (s2 ** 2).sum()) + 0.0
+
+
+# --------------------------------------------------- gradient (FD identity) --
+def _fd_scene(air):
+    n = 4
+    rng = np.random.default_rng(21 + air)
+    beta = rng.uniform(2.0, 12.0, size=(n, n, n)).astype(np.float32)
+    return synth.Scene(name="fd", n=(n, n, n), voxel=0.04, beta_cloud=beta,
+                       beta_air=0.6 if air else 0.0, albedo_air=0.9, albedo_cloud=0.95,
+                       cameras=synth.arc_cameras(2, (0.16,) * 3, 4, 4),
+                       n_paths=1 << 11, seed=77)
+
+
+@pytest.mark.parametrize("air", [0, 1])
+def test_gradient_equals_finite_difference_4cubed(air):
+    """P-f: with paths fixed, F(M_t | M_ref) is smooth in M_t and the paper's
+    recycled gradient estimator (Eq. 21 with the PSF of Sec. 4.4) is its exact
+    derivative; central differences of the FP64 loss on every voxel of a 4^3
+    grid (brute force), with air (two particle types) and without."""
+    sc = _fd_scene(air)
+    rng = np.random.default_rng(5)
+    bref = sc.beta_cloud
+    bt = (bref * rng.uniform(0.85, 1.2, size=bref.shape)).astype(np.float32)
+    igt = 0.7 * O.render(sc, bref, seed=999)["images"]
+
+    def loss(b):
+        F = O.render(sc, bref, b)["images"]
+        return 0.5 * np.sum((F - igt) ** 2)
+
+    F = O.render(sc, bref, bt)["images"]
+    r = O.render(sc, bref, bt, dldi=F - igt, grad_abs=True)
+    g, ga = r["grad"], r["grad_abs"]
+    flat = bt.reshape(-1)
+    assert np.abs(g).max() > 0
+    for v in range(flat.size):
+        bp = flat.copy(); bm = flat.copy()
+        bp[v] = np.float32(flat[v] * (1 + 1e-3)); bm[v] = np.float32(flat[v] * (1 - 1e-3))
+        fd = (loss(bp) - loss(bm)) / (float(bp[v]) - float(bm[v]))
+        assert abs(fd - g[v]) <= 1e-6 * ga[v] + 1e-14, (v, fd, g[v], ga[v])
+
+
+def test_threads_do_not_change_results():
+    sc = synth.config(1, n_paths=1 << 11)
+    a = O.render(sc, sc.beta_cloud, threads=1)["images"]
+    b = O.render(sc, sc.beta_cloud, threads=4)["images"]
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-15)
+
+
+def test_fingerprints_identify_paths():
+    sc = synth.config(1, n_paths=1 << 10)
+    f1 = O.render(sc, sc.beta_cloud, fingerprints=True)["fingerprints"]
+    f2 = O.render(sc, sc.beta_cloud, fingerprints=True)["fingerprints"]
+    f3 = O.render(sc, sc.beta_cloud, fingerprints=True, seed=sc.seed + 1)["fingerprints"]
+    assert np.array_equal(f1, f2)
+    # paths that never collide share one fingerprint; the rest are distinct
+    assert np.mean(f1 != f3) > 0.25
+    assert len(np.unique(f1)) > 0.25 * len(f1)
