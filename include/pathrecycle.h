@@ -1,0 +1,214 @@
+/*
+ * pathrecycle.h -- C ABI of libpathrecycle.so: Monte-Carlo scattering
+ * tomography with path recycling on one GB300 (sm_103a).
+ *
+ * Method: Czerninski & Schechner, "Accelerating Inverse Rendering By Using
+ * a GPU and Reuse of Light Paths" (arXiv 2110.00085).
+ *   - forward model: path tracing through a voxel grid of extinction with a
+ *     directional sun, free-path (distance) sampling, particle-type and
+ *     direction sampling, and local estimation toward every camera pixel
+ *     (Sec. 3.4, Eq. Qd; scene of Sec. 6.1);
+ *   - loss and gradient: L = 1/2 ||F - I_gt||^2 (Eq. appearance_loss), its
+ *     gradient through the path score function (Eqs. loss_gradient,
+ *     gradient_simualtion; PSF of scattering tomography, Sec. 4.4);
+ *   - path recycling: stored paths reweighted by f(x|M_t)/mu(x|M_ref)
+ *     (Sec. 5.2, Eqs. forward_simualtion_recycling, correction factor,
+ *     gradient_simualtion_recycling) and sorted by path size (Sec. 5.3).
+ *
+ * Conventions shared by every call
+ *   - Units: km and 1/km.  Grids are float32, x fastest (index
+ *     x + nx*(y + ny*z)), nx*ny*nz < 2^28.
+ *   - Images are float64, camera after camera, each row-major W x H with
+ *     row 0 at the top; pixel values are radiance averaged over the pixel's
+ *     solid angle, for unit sun irradiance times sun_irradiance.
+ *   - All device pointers are CUDA device memory of the current device and
+ *     are owned by the caller unless stated otherwise; `stream` is a
+ *     cudaStream_t (NULL = legacy default stream).  Every call is
+ *     asynchronous on `stream` except where stated.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = seed
+ *     and counter (path id lo, path id hi, event | tag << 8 | epoch << 16,
+ *     scene id); uniforms u = ((w >> 8) + 1) * 2^-24 in (0, 1].
+ *   - Return value: PT_OK or a PT_E_* code; the message of the latest
+ *     failure on the calling thread is pt_last_error().  No call aborts the
+ *     process.  Kernel-side invariant violations are recorded in the handle
+ *     and reported by pt_check().
+ */
+#ifndef PATHRECYCLE_H
+#define PATHRECYCLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PT_OK 0
+#define PT_E_INVALID 1        /* bad argument or handle                     */
+#define PT_E_OOM 2            /* device allocation failed                   */
+#define PT_E_CUDA 3           /* a CUDA runtime call failed                 */
+#define PT_E_TIMEOUT 4        /* a bounded device-side wait gave up         */
+#define PT_E_DEVICE_ASSERT 5  /* a kernel detected a violated invariant     */
+
+#define PT_MAX_CAMS 64
+#define PT_MAX_ORDERS 15
+
+/* flags */
+#define PT_ACCUMULATE 1u      /* add into the outputs instead of zeroing them */
+#define PT_CACHE 2u           /* paths_reweight: keep per-(event, camera)
+                                 contributions in the handle; render_grad: use
+                                 them instead of re-tracing shadow rays (the
+                                 caller guarantees beta_t is unchanged)        */
+
+/* tallies: float64[PT_TALLY_COUNT], same meaning as the CPU oracle's */
+enum {
+    PT_T_INJECTED = 0, PT_T_MISSED, PT_T_ESCAPED, PT_T_ABSORBED, PT_T_TRUNCATED,
+    PT_T_RR_KILLED, PT_T_RR_GAIN, PT_T_COLLISIONS, PT_T_ENTERED, PT_T_SEG_CROSS,
+    PT_T_SHADOW_CROSS, PT_T_IN_VIEW, PT_TALLY_COUNT
+};
+
+/* Perspective pinhole camera.  The image plane sits at unit distance along
+ * normalize(look_at - pos); right = normalize(forward x up), image-up =
+ * right x forward; fov_y is the full vertical field of view (radians);
+ * pixels are square.  Pixel response (a reading of the pixel response W_d of
+ * Sec. 3.3 for a perspective pixel): 1 / (exact solid angle of the pixel). */
+typedef struct {
+    float pos[3];
+    float look_at[3];
+    float up[3];
+    float fov_y;
+    int32_t width, height;
+} pt_camera;
+
+/* Scene of scattering tomography (Sec. 4.4, Sec. 6.1): cloud droplets with
+ * unknown extinction (passed per call), albedo_cloud and a Henyey-Greenstein
+ * phase function of asymmetry hg_g; air with known uniform extinction
+ * beta_air, albedo_air and a Rayleigh phase function; a sun with parallel
+ * rays travelling along the unit vector sun_dir with irradiance
+ * sun_irradiance.  Paths stop after max_orders collisions (<= PT_MAX_ORDERS)
+ * and after collision k >= rr_start survive Russian roulette with
+ * probability rr_q (weight / rr_q). */
+typedef struct {
+    int32_t nx, ny, nz;
+    float voxel;                 /* km, cubic voxels                  */
+    float origin[3];             /* km, corner of voxel (0,0,0)       */
+    float beta_air, albedo_cloud, albedo_air, hg_g;
+    float sun_dir[3];
+    float sun_irradiance;
+    int32_t n_cams;              /* 1 .. PT_MAX_CAMS                  */
+    const pt_camera* cams;       /* host array, copied by pt_scene_create */
+    int32_t max_orders, rr_start;
+    float rr_q;                  /* (0, 1]                            */
+    uint32_t scene_id;           /* Philox counter word 3             */
+} pt_scene_desc;
+
+typedef struct pt_scene pt_scene;   /* device-resident scene constants      */
+typedef struct pt_paths pt_paths;   /* stored, size-sorted light paths      */
+
+typedef struct {
+    uint64_t n_paths;        /* paths sampled by the latest paths_store      */
+    uint64_t n_stored;       /* of which stored (at least one collision)     */
+    uint64_t n_records;      /* stored vertices (sum of B+1)                 */
+    uint64_t bucket[PT_MAX_ORDERS + 1];   /* paths per path size B           */
+    uint64_t bytes_device;   /* device memory held by the handle            */
+} pt_paths_info;
+
+/* Create a scene on the current device: copies the cameras, computes every
+ * pixel's solid angle (float64 arithmetic, stored float32) and the sun's
+ * sampling rectangle.  Synchronous.  Owner: the caller frees it with
+ * pt_scene_free after every handle that uses it. */
+int pt_scene_create(const pt_scene_desc* desc, pt_scene** out);
+int pt_scene_free(pt_scene* scene);
+int64_t pt_scene_pixels(const pt_scene* scene);
+
+/*
+ * render_forward -- plain path tracing (Alg. 1 forward step; estimator of
+ * Eq. forward_simualtion with local estimation, Eq. Qd).
+ * Traces paths first_path .. first_path+n_paths-1 under beta_cloud (device,
+ * nx*ny*nz) and adds sum(contributions) / n_norm into images (device,
+ * pt_scene_pixels doubles; zeroed first unless PT_ACCUMULATE).
+ * tallies (device, PT_TALLY_COUNT doubles, accumulated) and fingerprints
+ * (device, n_paths uint64: FNV-1a of each path's discrete decisions) may be
+ * NULL.
+ */
+int render_forward(const pt_scene* scene, const float* beta_cloud,
+                   uint64_t first_path, uint64_t n_paths, double n_norm,
+                   uint64_t seed, uint32_t epoch, double* images, uint32_t flags,
+                   double* tallies, uint64_t* fingerprints, void* stream);
+
+/*
+ * paths_store -- sample, sort and store light paths (Alg. 2, the resample
+ * branch: sample under M_t, sort by path size, set M_ref <- M_t).
+ * Traces the same paths as render_forward would and keeps every path with at
+ * least one collision, counting-sorted by its number of collisions B
+ * (stable in path id), as compact vertex records.  The handle keeps a copy
+ * of beta_cloud as M_ref.  *paths == NULL creates a handle (owned by the
+ * caller, freed with paths_free); an existing handle of the same scene is
+ * reused, growing its buffers if n_paths exceeds its capacity.  images_ref
+ * (nullable) receives the plain estimate under M_ref (as render_forward).
+ * Allocation (first use or growth) synchronises the device.
+ */
+int paths_store(const pt_scene* scene, const float* beta_cloud,
+                uint64_t first_path, uint64_t n_paths, double n_norm,
+                uint64_t seed, uint32_t epoch, pt_paths** paths,
+                double* images_ref, uint32_t flags, double* tallies,
+                uint64_t* fingerprints, void* stream);
+
+/*
+ * paths_reweight -- recycled forward model F(M_t | M_ref) (Eqs.
+ * forward_simualtion_recycling and correction factor): every event of every
+ * stored path contributes f(x|M_t)/mu(x|M_ref), i.e. its contribution under
+ * beta_t times the ratio of path pdfs under beta_t and the stored M_ref.
+ * beta_t: device grid; images as in render_forward, divided by the n_norm of
+ * the store.  With PT_CACHE the per-(event, camera) contributions are kept
+ * in the handle for render_grad.
+ */
+int paths_reweight(pt_paths* paths, const float* beta_t, double* images,
+                   uint32_t flags, void* stream);
+
+/*
+ * render_grad -- gradient of the loss with respect to the cloud extinction
+ * (Eq. loss_gradient with the recycled estimator of Eq.
+ * gradient_simualtion_recycling and the path score function of Sec. 4.4):
+ * grad[v] += sum over events and cameras of dL_dI[pixel] * contribution *
+ * score_v.  dL_dI: device, images layout (e.g. F - I_gt); grad: device,
+ * nx*ny*nz doubles, zeroed first unless PT_ACCUMULATE.  With PT_CACHE the
+ * contributions come from the latest paths_reweight (which must have been
+ * called with PT_CACHE and the same beta_t).
+ */
+int render_grad(pt_paths* paths, const float* beta_t, const double* dL_dI,
+                double* grad, uint32_t flags, void* stream);
+
+int paths_free(pt_paths* paths);
+/* Synchronises the stream; fills counts of the latest store. */
+int paths_info(const pt_paths* paths, pt_paths_info* out, void* stream);
+
+/*
+ * adam_step -- Adam (Kingma & Ba; moment decays b1, b2, step lr, epsilon
+ * eps, step number t >= 1) on the cloud extinction with the projection
+ * beta >= 0 (Sec. 6: a modified Adam; the modification is not given, the
+ * projection keeps extinction physical).  beta, m, v: device float32[n];
+ * grad: device float64[n].
+ */
+int adam_step(float* beta, float* m, float* v, const double* grad, int64_t n,
+              int32_t t, float lr, float b1, float b2, float eps, void* stream);
+
+/*
+ * loss_residual -- dL_dI = images - gt and *loss = 1/2 sum (images - gt)^2
+ * (Eq. appearance_loss).  All device float64; loss is one double, written
+ * (not accumulated).
+ */
+int loss_residual(const double* images, const double* gt, int64_t n,
+                  double* dL_dI, double* loss, void* stream);
+
+/* Synchronises the stream and reports (then clears) kernel-side invariant
+ * violations recorded in the scene. */
+int pt_check(const pt_scene* scene, void* stream);
+
+const char* pt_last_error(void);
+const char* pt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PATHRECYCLE_H */

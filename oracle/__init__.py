@@ -88,7 +88,7 @@ def lib():
             L.or_intervals.argtypes = [C.POINTER(ORScene), _dp, _dp, C.c_double, _i64p, _dp, C.c_int]
             L.or_intervals.restype = C.c_int
             L.or_render.argtypes = [C.POINTER(ORScene), _fp, _fp, C.c_uint64, C.c_uint64, C.c_double,
-                                    _dp, _dp, _dp, _dp, _dp, _u64p, C.c_int]
+                                    _dp, _dp, _dp, _dp, _dp, _dp, _u64p, C.c_int]
             L.or_render.restype = C.c_int
             L.or_path.argtypes = [C.POINTER(ORScene), _fp, C.c_uint64, _dp, _dp, _i64p, _dp, C.POINTER(C.c_int)]
             L.or_path.restype = C.c_int
@@ -108,12 +108,16 @@ class OScene:
     """Keeps the ctypes struct and the arrays it points into alive."""
 
     def __init__(self, sc, epoch: int = 0, scene_id: int = 0, seed=None):
+        # Scene constants are taken at float32 precision, the precision in
+        # which the scene is specified to the library under test; the
+        # oracle's arithmetic on them is float64.
+        f32 = lambda v: float(np.float32(v))
         cams = np.zeros((len(sc.cameras), 12), dtype=np.float64)
         for i, c in enumerate(sc.cameras):
-            cams[i, 0:3] = c.pos
-            cams[i, 3:6] = c.look_at
-            cams[i, 6:9] = c.up
-            cams[i, 9] = c.fov_y
+            cams[i, 0:3] = [f32(v) for v in c.pos]
+            cams[i, 3:6] = [f32(v) for v in c.look_at]
+            cams[i, 6:9] = [f32(v) for v in c.up]
+            cams[i, 9] = f32(c.fov_y)
             cams[i, 10] = c.width
             cams[i, 11] = c.height
         self.cams = np.ascontiguousarray(cams)
@@ -125,16 +129,18 @@ class OScene:
         s.epoch = int(epoch)
         s.scene_id = int(scene_id)
         s.seed = int(sc.seed if seed is None else seed)
-        s.voxel = float(sc.voxel)
+        s.voxel = f32(sc.voxel)
+        sun = np.array([f32(v) for v in sc.sun_dir], dtype=np.float64)
+        sun /= np.linalg.norm(sun)
         for i in range(3):
-            s.origin[i] = float(sc.origin[i])
-            s.sun[i] = float(sc.sun_dir[i])
-        s.beta_air = float(sc.beta_air)
-        s.albedo_cloud = float(sc.albedo_cloud)
-        s.albedo_air = float(sc.albedo_air)
-        s.hg_g = float(sc.hg_g)
-        s.sun_irradiance = float(sc.sun_irradiance)
-        s.rr_q = float(sc.rr_q)
+            s.origin[i] = f32(sc.origin[i])
+            s.sun[i] = float(sun[i])
+        s.beta_air = f32(sc.beta_air)
+        s.albedo_cloud = f32(sc.albedo_cloud)
+        s.albedo_air = f32(sc.albedo_air)
+        s.hg_g = f32(sc.hg_g)
+        s.sun_irradiance = f32(sc.sun_irradiance)
+        s.rr_q = f32(sc.rr_q)
         s.cams = self.cams.ctypes.data_as(_dp)
         self.s = s
         self.n_pixels = int(sum(c.width * c.height for c in sc.cameras))
@@ -150,12 +156,19 @@ def _grid(b):
 
 
 def render(sc, beta_ref, beta_t=None, first: int = 0, n=None, n_norm=None, dldi=None,
-           grad_abs: bool = False, tallies: bool = False, fingerprints: bool = False,
+           grad_abs: bool = False, grad_cond: bool = False, tallies: bool = False, fingerprints: bool = False,
            threads: int = 1, epoch: int = 0, scene_id: int = 0, seed=None):
     """Paths [first, first+n) sampled under ``beta_ref``, evaluated under
     ``beta_t`` (default: the same grid).  Returns a dict with ``images``
     (float64, n_pixels), and when asked ``grad``/``grad_abs`` (float64,
-    n_voxels), ``tallies`` (dict) and ``fingerprints`` (uint64, n)."""
+    n_voxels), ``grad_cond`` (per voxel, an error budget for float32
+    implementations: sum over its length terms of |dL/dI * contribution|
+    times the length's conditioning (1/|d_axis| per bounding face) times how
+    far a float32 computation of the ray's origin vertex may lie from the
+    float64 one -- a few units of roundoff of the coordinates, plus
+    u (tau + 1) / beta for a collision point, which is ill-conditioned
+    where the extinction is small),
+    ``tallies`` (dict) and ``fingerprints`` (uint64, n)."""
     L = lib()
     os_ = OScene(sc, epoch=epoch, scene_id=scene_id, seed=seed)
     n = int(sc.n_paths if n is None else n)
@@ -164,7 +177,7 @@ def render(sc, beta_ref, beta_t=None, first: int = 0, n=None, n_norm=None, dldi=
     bt = br if beta_t is None else _grid(beta_t)
     img = np.zeros(os_.n_pixels, dtype=np.float64)
     out = {"images": img}
-    g = ga = dl = None
+    g = ga = gc = dl = None
     if dldi is not None:
         dl = np.ascontiguousarray(np.asarray(dldi, dtype=np.float64).reshape(-1))
         g = np.zeros(os_.n_voxels, dtype=np.float64)
@@ -172,11 +185,14 @@ def render(sc, beta_ref, beta_t=None, first: int = 0, n=None, n_norm=None, dldi=
         if grad_abs:
             ga = np.zeros(os_.n_voxels, dtype=np.float64)
             out["grad_abs"] = ga
+        if grad_cond:
+            gc = np.zeros(os_.n_voxels, dtype=np.float64)
+            out["grad_cond"] = gc
     tal = np.zeros(L.or_tally_count(), dtype=np.float64) if tallies else None
     fp = np.zeros(n, dtype=np.uint64) if fingerprints else None
     rc = L.or_render(os_.ref, _ptr(br, _fp), _ptr(bt, _fp), C.c_uint64(first), C.c_uint64(n),
                      C.c_double(n_norm), _ptr(img, _dp), _ptr(dl, _dp), _ptr(g, _dp), _ptr(ga, _dp),
-                     _ptr(tal, _dp), _ptr(fp, _u64p), int(threads))
+                     _ptr(gc, _dp), _ptr(tal, _dp), _ptr(fp, _u64p), int(threads))
     if rc != 0:
         raise RuntimeError(f"or_render failed ({rc})")
     if tal is not None:

@@ -216,19 +216,24 @@ void or_rotate(const double d[3], double mu, double phi, double out[3])
 /* 4.4 (Fig. inverse_notations) computed by brute force: every face         */
 /* crossing is listed and the list sorted.                                  */
 /* ------------------------------------------------------------------------ */
-typedef struct { int64_t v; double t0, t1; } ivl;
+typedef struct { int64_t v; double t0, t1; int a0, a1; } ivl;
+typedef struct { double t; int axis; } tcut;   /* a face crossing and its axis (-1: segment end) */
 
-static int cmp_double(const void* a, const void* b)
+static int cmp_cut(const void* a, const void* b)
 {
-    double x = *(const double*)a, y = *(const double*)b;
+    double x = ((const tcut*)a)->t, y = ((const tcut*)b)->t;
     return (x < y) ? -1 : (x > y) ? 1 : 0;
 }
 
-/* clip [0, tmax] to the box; returns 0 when the segment misses it */
-static int clip_box(const or_scene* s, const double p[3], const double d[3], double tmax, double* ta, double* tb)
+/* clip [0, tmax] to the box; returns 0 when the segment misses it.  The
+ * axes of the box faces that bound the clipped range go to *aa, *ab (-1 when
+ * the range ends at the segment's own ends). */
+static int clip_box_axes(const or_scene* s, const double p[3], const double d[3], double tmax, double* ta,
+                         double* tb, int* aa, int* ab)
 {
     const int n[3] = {s->nx, s->ny, s->nz};
     double t0 = 0.0, t1 = tmax;
+    int a0 = -1, a1 = -1;
     for (int a = 0; a < 3; ++a) {
         double lo = s->origin[a], hi = s->origin[a] + n[a] * s->voxel;
         if (d[a] == 0.0) {
@@ -237,23 +242,30 @@ static int clip_box(const or_scene* s, const double p[3], const double d[3], dou
         }
         double u0 = (lo - p[a]) / d[a], u1 = (hi - p[a]) / d[a];
         if (u0 > u1) { double tmp = u0; u0 = u1; u1 = tmp; }
-        if (u0 > t0) t0 = u0;
-        if (u1 < t1) t1 = u1;
+        if (u0 > t0) { t0 = u0; a0 = a; }
+        if (u1 < t1) { t1 = u1; a1 = a; }
     }
     if (!(t1 > t0)) return 0;
     *ta = t0; *tb = t1;
+    if (aa) *aa = a0;
+    if (ab) *ab = a1;
     return 1;
+}
+static int clip_box(const or_scene* s, const double p[3], const double d[3], double tmax, double* ta, double* tb)
+{
+    return clip_box_axes(s, p, d, tmax, ta, tb, NULL, NULL);
 }
 
 /* list the voxel intervals of p + t d on [0, tmax]; out must hold nx+ny+nz+4 */
-static int intervals(const or_scene* s, const double p[3], const double d[3], double tmax, ivl* out, double* tbuf)
+static int intervals(const or_scene* s, const double p[3], const double d[3], double tmax, ivl* out, tcut* tbuf)
 {
     const int n[3] = {s->nx, s->ny, s->nz};
     double ta, tb;
-    if (!clip_box(s, p, d, tmax, &ta, &tb)) return 0;
+    int aa, ab;
+    if (!clip_box_axes(s, p, d, tmax, &ta, &tb, &aa, &ab)) return 0;
     int m = 0;
-    tbuf[m++] = ta;
-    tbuf[m++] = tb;
+    tbuf[m].t = ta; tbuf[m++].axis = aa;
+    tbuf[m].t = tb; tbuf[m++].axis = ab;
     for (int a = 0; a < 3; ++a) {
         if (d[a] == 0.0) continue;
         double c0 = (p[a] + ta * d[a] - s->origin[a]) / s->voxel;
@@ -264,13 +276,13 @@ static int intervals(const or_scene* s, const double p[3], const double d[3], do
         if (k1 > n[a] - 1) k1 = n[a] - 1;
         for (long k = k0; k <= k1; ++k) {
             double t = (s->origin[a] + (double)k * s->voxel - p[a]) / d[a];
-            if (t > ta && t < tb) tbuf[m++] = t;
+            if (t > ta && t < tb) { tbuf[m].t = t; tbuf[m++].axis = a; }
         }
     }
-    qsort(tbuf, (size_t)m, sizeof(double), cmp_double);
+    qsort(tbuf, (size_t)m, sizeof(tcut), cmp_cut);
     int cnt = 0;
     for (int i = 0; i + 1 < m; ++i) {
-        double t0 = tbuf[i], t1 = tbuf[i + 1];
+        double t0 = tbuf[i].t, t1 = tbuf[i + 1].t;
         if (!(t1 > t0)) continue;
         double tm = 0.5 * (t0 + t1);
         int64_t idx[3];
@@ -283,6 +295,8 @@ static int intervals(const or_scene* s, const double p[3], const double d[3], do
         out[cnt].v = idx[0] + (int64_t)s->nx * (idx[1] + (int64_t)s->ny * idx[2]);
         out[cnt].t0 = t0;
         out[cnt].t1 = t1;
+        out[cnt].a0 = tbuf[i].axis;
+        out[cnt].a1 = tbuf[i + 1].axis;
         ++cnt;
     }
     return cnt;
@@ -304,7 +318,7 @@ static double optical_depth(const or_scene* s, const float* bc, const ivl* iv, i
 double or_transmittance(const or_scene* s, const float* bc, const double p[3], const double d[3], double tmax)
 {
     ivl* iv = (ivl*)malloc(sizeof(ivl) * (size_t)max_intervals(s));
-    double* tb = (double*)malloc(sizeof(double) * (size_t)max_intervals(s));
+    tcut* tb = (tcut*)malloc(sizeof(tcut) * (size_t)max_intervals(s));
     int n = intervals(s, p, d, tmax, iv, tb);
     double tau = optical_depth(s, bc, iv, n);
     free(iv); free(tb);
@@ -316,7 +330,7 @@ int or_intervals(const or_scene* s, const double p[3], const double d[3], double
                  int64_t* vox, double* len, int cap)
 {
     ivl* iv = (ivl*)malloc(sizeof(ivl) * (size_t)max_intervals(s));
-    double* tb = (double*)malloc(sizeof(double) * (size_t)max_intervals(s));
+    tcut* tb = (tcut*)malloc(sizeof(tcut) * (size_t)max_intervals(s));
     int n = intervals(s, p, d, tmax, iv, tb);
     if (n > cap) n = cap;
     for (int i = 0; i < n; ++i) { vox[i] = iv[i].v; len[i] = iv[i].t1 - iv[i].t0; }
@@ -440,6 +454,8 @@ typedef struct {
     double l[OR_MAXV];
     int64_t v[OR_MAXV];
     int type[OR_MAXV];       /* particle type chosen at x_k: 0 cloud, 1 air, 2 none */
+    double dpos[OR_MAXV];    /* error budget only: how far a float32 computation of
+                                x_k may sit from this float64 one (km) */
 } opath;
 
 typedef struct {
@@ -447,9 +463,9 @@ typedef struct {
     osun sun;
     ocam* cams;
     ivl* iv;
-    double* tb;
+    tcut* tb;
     ivl* iv2;
-    double* tb2;
+    tcut* tb2;
 } octx;
 
 /*
@@ -493,6 +509,16 @@ static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double
     P->v[0] = -1;
     P->l[0] = 0.0;
     P->type[0] = 2;
+    /* float32 position budget: unit roundoff u times the coordinate scale for
+     * every computed point, plus the collision point's sensitivity to the
+     * optical depth, u (tau + 1) / beta, where beta is small */
+    const double u32 = 1.0 / 16777216.0;
+    double Lsc = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const int na = a == 0 ? s->nx : a == 1 ? s->ny : s->nz;
+        Lsc = fmax(Lsc, fabs(s->origin[a]) + na * s->voxel);
+    }
+    P->dpos[0] = 8.0 * u32 * Lsc;
     double w = w0;
     double tau = -log(u[2]);
     for (int k = 1;; ++k) {
@@ -524,6 +550,7 @@ static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double
         P->v[k] = vcol;
         P->type[k] = 2;
         P->B = k;
+        P->dpos[k] = P->dpos[k - 1] + 8.0 * u32 * Lsc + 4.0 * u32 * (tau + 1.0) / beta_tot(s, bc, vcol);
         double bcv = (double)bc[vcol];
         double alb = beta_s(s, bcv) / beta_tot(s, bc, vcol);
         if (tal) { tal[T_COLLISIONS] += 1.0; tal[T_ABSORBED] += w * (1.0 - alb); }
@@ -593,15 +620,30 @@ static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double
  * sub-path.  Events with zero contribution are skipped (their score may be
  * infinite where beta_c = 0 and there is no air).
  */
+/* conditioning of an interval's length: how far its ends move along the
+ * ray per unit displacement of the ray normal to the faces that bound it
+ * (1 / |d_axis| per face end, 1 per segment end) */
+static double length_cond(const ivl* iv, const double d[3])
+{
+    double k0 = iv->a0 >= 0 ? 1.0 / fabs(d[iv->a0]) : 1.0;
+    double k1 = iv->a1 >= 0 ? 1.0 / fabs(d[iv->a1]) : 1.0;
+    return k0 + k1;
+}
+
 static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
                       double inv_norm, double* img, const double* dldi,
-                      double* grad, double* gabs, double* tal, uint64_t* fp)
+                      double* grad, double* gabs, double* gcond, double* tal, uint64_t* fp)
 {
     const or_scene* s = c->s;
+    /* fingerprint words: per event (voxel, pixel per camera, particle type),
+     * then the event count and the end type */
     uint64_t h = 0xcbf29ce484222325ull;
-    h = fnv_word(h, (uint32_t)P->B);
-    h = fnv_word(h, (uint32_t)P->end);
-    if (!P->entered) { if (fp) *fp = h; return; }
+    if (!P->entered) {
+        h = fnv_word(h, 0u);
+        h = fnv_word(h, (uint32_t)P->end);
+        if (fp) *fp = h;
+        return;
+    }
     double w0 = s->sun_irradiance * c->sun.area;
     double log_tr = 0.0;       /* sum over flights of tau_ref - tau_t */
     double vert = 1.0;         /* product of the vertex ratios k < b  */
@@ -625,7 +667,6 @@ static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
         double base = w0 * exp(log_tr) * vert * pow(s->rr_q, -(double)nrr);
         int64_t vb = P->v[b];
         h = fnv_word(h, (uint32_t)vb);
-        h = fnv_word(h, (uint32_t)P->type[b]);
         for (int d = 0; d < s->n_cams; ++d) {
             const ocam* k = &c->cams[d];
             int col, row;
@@ -653,6 +694,9 @@ static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
                     double t = A * (c->iv[i].t1 - c->iv[i].t0);
                     grad[c->iv[i].v] -= t;
                     if (gabs) gabs[c->iv[i].v] += fabs(t);
+                    if (gcond)
+                        gcond[c->iv[i].v] += fabs(A) * length_cond(&c->iv[i], P->om[j - 1]) *
+                                             fmax(P->dpos[j - 1], P->dpos[j]);
                 }
             }
             /* shadow ray x_b -> camera */
@@ -660,6 +704,7 @@ static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
                 double t = A * (c->iv2[i].t1 - c->iv2[i].t0);
                 grad[c->iv2[i].v] -= t;
                 if (gabs) gabs[c->iv2[i].v] += fabs(t);
+                if (gcond) gcond[c->iv2[i].v] += fabs(A) * length_cond(&c->iv2[i], dir) * P->dpos[b];
             }
             /* scattering vertices 1..b-1 (angle between sampled directions) */
             for (int j = 1; j < b; ++j) {
@@ -676,7 +721,10 @@ static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
                 if (gabs) gabs[vb] += fabs(t);
             }
         }
+        h = fnv_word(h, (uint32_t)P->type[b]);
     }
+    h = fnv_word(h, (uint32_t)P->B);
+    h = fnv_word(h, (uint32_t)P->end);
     if (fp) *fp = h;
 }
 
@@ -700,7 +748,7 @@ static int64_t total_pixels(const or_scene* s)
 int or_render(const or_scene* s, const float* beta_ref, const float* beta_t,
               uint64_t first_path, uint64_t n_paths, double n_norm,
               double* images, const double* dldi, double* grad, double* gabs,
-              double* tallies, uint64_t* fingerprints, int threads)
+              double* gcond, double* tallies, uint64_t* fingerprints, int threads)
 {
     if (s->max_orders + 1 >= OR_MAXV || s->max_orders < 1) return -1;
     int64_t npix = total_pixels(s);
@@ -727,24 +775,26 @@ int or_render(const or_scene* s, const float* beta_ref, const float* beta_t,
         setup_cams(s, c.cams);
         int mi = max_intervals(s);
         c.iv = (ivl*)malloc(sizeof(ivl) * (size_t)mi);
-        c.tb = (double*)malloc(sizeof(double) * (size_t)mi);
+        c.tb = (tcut*)malloc(sizeof(tcut) * (size_t)mi);
         c.iv2 = (ivl*)malloc(sizeof(ivl) * (size_t)mi);
-        c.tb2 = (double*)malloc(sizeof(double) * (size_t)mi);
+        c.tb2 = (tcut*)malloc(sizeof(tcut) * (size_t)mi);
         opath* P = (opath*)malloc(sizeof(opath));
         double* img = images;
         double* g = grad;
         double* ga = gabs;
+        double* gc = gcond;
         double tal[T_COUNT];
         memset(tal, 0, sizeof(tal));
         if (nt > 1) {
             img = images ? (double*)calloc((size_t)npix, sizeof(double)) : NULL;
             g = grad ? (double*)calloc((size_t)nvox, sizeof(double)) : NULL;
             ga = gabs ? (double*)calloc((size_t)nvox, sizeof(double)) : NULL;
+            gc = gcond ? (double*)calloc((size_t)nvox, sizeof(double)) : NULL;
         }
         for (uint64_t i = (uint64_t)tid; i < n_paths; i += (uint64_t)nt) {
             uint64_t pid = first_path + i;
             sample_path(&c, beta_ref, pid, P, tal);
-            eval_path(&c, beta_ref, beta_t, P, inv_norm, img, dldi, g, ga, tal,
+            eval_path(&c, beta_ref, beta_t, P, inv_norm, img, dldi, g, ga, gc, tal,
                       fingerprints ? &fingerprints[i] : NULL);
         }
 #ifdef _OPENMP
@@ -755,10 +805,11 @@ int or_render(const or_scene* s, const float* beta_ref, const float* beta_t,
                 if (img) for (int64_t j = 0; j < npix; ++j) images[j] += img[j];
                 if (g) for (int64_t j = 0; j < nvox; ++j) grad[j] += g[j];
                 if (ga) for (int64_t j = 0; j < nvox; ++j) gabs[j] += ga[j];
+                if (gc) for (int64_t j = 0; j < nvox; ++j) gcond[j] += gc[j];
             }
             if (tallies) for (int j = 0; j < T_COUNT; ++j) tallies[j] += tal[j];
         }
-        if (nt > 1) { free(img); free(g); free(ga); }
+        if (nt > 1) { free(img); free(g); free(ga); free(gc); }
         free(P); free(c.iv); free(c.tb); free(c.iv2); free(c.tb2); free(c.cams);
     }
     return err;
@@ -773,7 +824,7 @@ int or_path(const or_scene* s, const float* beta, uint64_t pid, double* x, doubl
     int mi = max_intervals(s);
     c.cams = NULL;
     c.iv = (ivl*)malloc(sizeof(ivl) * (size_t)mi);
-    c.tb = (double*)malloc(sizeof(double) * (size_t)mi);
+    c.tb = (tcut*)malloc(sizeof(tcut) * (size_t)mi);
     opath* P = (opath*)malloc(sizeof(opath));
     sample_path(&c, beta, pid, P, NULL);
     int B = P->entered ? P->B : -1;
@@ -817,9 +868,9 @@ void or_single_scatter_quad(const or_scene* s, const float* bc, int sub, int ste
 #endif
         for (int64_t pix = 0; pix < npx; ++pix) {
             ivl* iv = (ivl*)malloc(sizeof(ivl) * (size_t)mi);
-            double* tb = (double*)malloc(sizeof(double) * (size_t)mi);
+            tcut* tb = (tcut*)malloc(sizeof(tcut) * (size_t)mi);
             ivl* iv2 = (ivl*)malloc(sizeof(ivl) * (size_t)mi);
-            double* tb2 = (double*)malloc(sizeof(double) * (size_t)mi);
+            tcut* tb2 = (tcut*)malloc(sizeof(tcut) * (size_t)mi);
             int col = (int)(pix % k->W), row = (int)(pix / k->W);
             double num = 0.0, den = 0.0;
             for (int i = 0; i < sub; ++i) {

@@ -1,0 +1,479 @@
+// pt_api.cu -- the C ABI of libpathrecycle (declared in include/pathrecycle.h):
+// argument checks, handle lifetime, device buffers, and the small
+// element-wise kernels (pixel solid angles, grid difference, loss residual,
+// Adam).  Every call launches on the caller's stream; errors are returned,
+// never raised, and described by pt_last_error().
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pt_kernels.cuh"
+
+using namespace pt;
+
+// ------------------------------------------------------------ errors -----
+namespace {
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define PT_CUDA(call)                                                                                \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return fail(PT_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));      \
+    } while (0)
+
+int launch_status(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(PT_E_CUDA, "%s launch: %s", what, cudaGetErrorString(e));
+    return PT_OK;
+}
+
+cudaStream_t S_(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ------------------------------------------------ small kernels ---------
+// exact solid angle of each pixel (float64 arithmetic): signed corner sums of
+// F(x, y) = atan(x y / sqrt(1 + x^2 + y^2)) on the unit-distance image plane
+__global__ void k_pixel_omega(const DevCam* cams, int n_cams, const double* tans, float* omega, int64_t npix) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= npix) return;
+    int c = 0;
+    while (c + 1 < n_cams && g >= cams[c + 1].off) ++c;
+    const DevCam& k = cams[c];
+    const int64_t p = g - k.off;
+    const int col = (int)(p % k.W), row = (int)(p / k.W);
+    const double tx = tans[2 * c], ty = tans[2 * c + 1];
+    const double xa = tx * (-1.0 + 2.0 * col / (double)k.W), xb = tx * (-1.0 + 2.0 * (col + 1) / (double)k.W);
+    const double ya = ty * (1.0 - 2.0 * (row + 1) / (double)k.H), yb = ty * (1.0 - 2.0 * row / (double)k.H);
+    auto F = [](double x, double y) { return atan(x * y / sqrt(1.0 + x * x + y * y)); };
+    omega[g] = (float)(F(xb, yb) - F(xa, yb) - F(xb, ya) + F(xa, ya));
+}
+
+__global__ void k_resid(const double* __restrict__ img, const double* __restrict__ gt, int64_t n,
+                        double* __restrict__ r, double* __restrict__ loss) {
+    __shared__ double part[256];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = img[i] - gt[i];
+        r[i] = d;
+        s += d * d;
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && loss) atomicAdd(loss, 0.5 * part[0]);
+}
+
+__global__ void k_adam(float* __restrict__ beta, float* __restrict__ m, float* __restrict__ v,
+                       const double* __restrict__ g, int64_t n, float lr, float b1, float b2, float eps,
+                       float inv_bc1, float inv_bc2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = __double2float_rn(g[i]);
+        const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
+        const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
+        m[i] = mi;
+        v[i] = vi;
+        const float step = lr * (mi * inv_bc1) / (sqrtf(vi * inv_bc2) + eps);
+        beta[i] = fmaxf(beta[i] - step, 0.0f);
+    }
+}
+
+unsigned grid_for(int64_t n, int bs, int cap = 152 * 32) {
+    int64_t g = (n + bs - 1) / bs;
+    if (g > cap) g = cap;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+// ---------------------------------------------------- host geometry -----
+void cross(const double* a, const double* b, double* o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+bool normalize(double* a) {
+    const double n = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    if (!(n > 0.0) || !std::isfinite(n)) return false;
+    a[0] /= n; a[1] /= n; a[2] /= n;
+    return true;
+}
+}  // namespace
+
+// ------------------------------------------------------------ handles ----
+struct pt_scene {
+    DevScene ds;
+    DevCam* d_cams = nullptr;
+    float* d_omega = nullptr;
+    int* d_err = nullptr;
+    int64_t n_pixels = 0;
+};
+
+struct pt_paths {
+    const pt_scene* scene = nullptr;
+    uint64_t cap = 0;          // paths per store
+    uint64_t n = 0;            // paths of the latest store
+    int slots = 0;             // max_orders + 1
+    float inv_norm = 1.0f;
+    int64_t V = 0;
+    float* beta_ref = nullptr;
+    float* dbeta = nullptr;
+    uint4* ua = nullptr;
+    float4* ub = nullptr;
+    uint8_t* cnt = nullptr;
+    uint4* sa = nullptr;
+    float4* sb = nullptr;
+    uint32_t* blk = nullptr;
+    Buckets* bk = nullptr;
+    float* cache = nullptr;
+    uint64_t cache_cap = 0;    // floats
+    uint64_t bytes = 0;
+    bool cache_valid = false;
+};
+
+namespace {
+void free_paths_buffers(pt_paths* p) {
+    cudaFree(p->beta_ref); cudaFree(p->dbeta); cudaFree(p->ua); cudaFree(p->ub); cudaFree(p->cnt);
+    cudaFree(p->sa); cudaFree(p->sb); cudaFree(p->blk); cudaFree(p->bk); cudaFree(p->cache);
+    p->beta_ref = p->dbeta = nullptr; p->ua = p->sa = nullptr; p->ub = p->sb = nullptr; p->cnt = nullptr;
+    p->blk = nullptr; p->bk = nullptr; p->cache = nullptr; p->cache_cap = 0; p->cap = 0; p->bytes = 0;
+}
+
+template <class T>
+int dev_alloc(T** p, uint64_t count, uint64_t* bytes, const char* what) {
+    const size_t b = (size_t)count * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)p, b ? b : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(PT_E_OOM, "cudaMalloc(%s, %zu bytes): %s", what, b, cudaGetErrorString(e));
+    }
+    if (bytes) *bytes += b;
+    return PT_OK;
+}
+
+SortedPaths sorted_view(const pt_paths* p) {
+    SortedPaths s;
+    s.rec_a = p->sa;
+    s.rec_b = p->sb;
+    s.buckets = p->bk;
+    s.n_max = p->n;
+    s.inv_norm = p->inv_norm;
+    return s;
+}
+}  // namespace
+
+extern "C" {
+
+const char* pt_last_error(void) { return g_err; }
+const char* pt_version(void) { return "pathrecycle 0.1 (sm_103a)"; }
+
+int pt_scene_create(const pt_scene_desc* d, pt_scene** out) {
+    if (!d || !out) return fail(PT_E_INVALID, "pt_scene_create: null argument");
+    *out = nullptr;
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(PT_E_INVALID, "grid dims must be >= 1");
+    const int64_t V = (int64_t)d->nx * d->ny * d->nz;
+    if (V >= (int64_t)1 << 28) return fail(PT_E_INVALID, "grid has %lld voxels; limit 2^28", (long long)V);
+    if (!(d->voxel > 0.0f) || !std::isfinite(d->voxel)) return fail(PT_E_INVALID, "voxel size must be > 0");
+    if (d->n_cams < 1 || d->n_cams > PT_MAX_CAMS || !d->cams)
+        return fail(PT_E_INVALID, "n_cams must be in 1..%d with a camera array", PT_MAX_CAMS);
+    if (d->max_orders < 1 || d->max_orders > PT_MAX_ORDERS)
+        return fail(PT_E_INVALID, "max_orders must be in 1..%d", PT_MAX_ORDERS);
+    if (!(d->rr_q > 0.0f && d->rr_q <= 1.0f)) return fail(PT_E_INVALID, "rr_q must be in (0, 1]");
+    if (!(d->beta_air >= 0.0f) || !(d->albedo_cloud >= 0.0f && d->albedo_cloud <= 1.0f) ||
+        !(d->albedo_air >= 0.0f && d->albedo_air <= 1.0f) || !(d->hg_g > -1.0f && d->hg_g < 1.0f))
+        return fail(PT_E_INVALID, "medium parameters out of range");
+    double s[3] = {d->sun_dir[0], d->sun_dir[1], d->sun_dir[2]};
+    if (!normalize(s)) return fail(PT_E_INVALID, "sun_dir must be a nonzero vector");
+
+    pt_scene* sc = new (std::nothrow) pt_scene();
+    if (!sc) return fail(PT_E_OOM, "host allocation");
+    DevScene& S = sc->ds;
+    memset(&S, 0, sizeof(S));
+    S.nx = d->nx; S.ny = d->ny; S.nz = d->nz; S.n_cams = d->n_cams; S.V = (int)V;
+    S.max_orders = d->max_orders; S.rr_start = d->rr_start; S.scene_id = d->scene_id;
+    S.vox = d->voxel; S.inv_vox = (float)(1.0 / (double)d->voxel);
+    S.ox = d->origin[0]; S.oy = d->origin[1]; S.oz = d->origin[2];
+    S.beta_air = d->beta_air; S.alb_c = d->albedo_cloud; S.alb_a = d->albedo_air; S.hg_g = d->hg_g;
+    const double g = d->hg_g;
+    S.hg_k = (float)((1.0 - g * g) / (4.0 * M_PI));
+    S.hg_1pg2 = (float)(1.0 + g * g);
+    S.hg_m2g = (float)(-2.0 * g);
+    S.sx = (float)s[0]; S.sy = (float)s[1]; S.sz = (float)s[2];
+    S.rr_q = d->rr_q; S.inv_q = (float)(1.0 / (double)d->rr_q);
+    // sun rectangle: basis of Duff et al. around s, projections of the corners
+    {
+        const double sign = std::copysign(1.0, s[2]);
+        const double a = -1.0 / (sign + s[2]);
+        const double b = s[0] * s[1] * a;
+        const double e1[3] = {1.0 + sign * s[0] * s[0] * a, sign * b, -sign * s[0]};
+        const double e2[3] = {b, sign + s[1] * s[1] * a, -s[1]};
+        double amin = INFINITY, amax = -INFINITY, bmin = INFINITY, bmax = -INFINITY, hmin = INFINITY;
+        const double L[3] = {d->nx * (double)d->voxel, d->ny * (double)d->voxel, d->nz * (double)d->voxel};
+        for (int c = 0; c < 8; ++c) {
+            double p[3];
+            for (int k = 0; k < 3; ++k) p[k] = d->origin[k] + ((c >> k) & 1) * L[k];
+            const double pa = p[0] * e1[0] + p[1] * e1[1] + p[2] * e1[2];
+            const double pb = p[0] * e2[0] + p[1] * e2[1] + p[2] * e2[2];
+            const double ph = p[0] * s[0] + p[1] * s[1] + p[2] * s[2];
+            amin = std::fmin(amin, pa); amax = std::fmax(amax, pa);
+            bmin = std::fmin(bmin, pb); bmax = std::fmax(bmax, pb);
+            hmin = std::fmin(hmin, ph);
+        }
+        for (int k = 0; k < 3; ++k) { S.e1[k] = (float)e1[k]; S.e2[k] = (float)e2[k]; }
+        S.amin = (float)amin; S.alen = (float)(amax - amin);
+        S.bmin = (float)bmin; S.blen = (float)(bmax - bmin);
+        S.hmin = (float)(hmin - 1.0);
+        S.w0 = (float)((double)d->sun_irradiance * (amax - amin) * (bmax - bmin));
+    }
+    // cameras
+    DevCam hc[PT_MAX_CAMS];
+    double tans[2 * PT_MAX_CAMS];
+    int64_t off = 0;
+    for (int c = 0; c < d->n_cams; ++c) {
+        const pt_camera& k = d->cams[c];
+        if (k.width < 1 || k.height < 1 || !(k.fov_y > 0.0f && k.fov_y < 3.1f)) {
+            delete sc;
+            return fail(PT_E_INVALID, "camera %d: bad size or field of view", c);
+        }
+        double F[3] = {(double)k.look_at[0] - k.pos[0], (double)k.look_at[1] - k.pos[1], (double)k.look_at[2] - k.pos[2]};
+        double up[3] = {k.up[0], k.up[1], k.up[2]};
+        double R[3], U[3];
+        if (!normalize(F)) { delete sc; return fail(PT_E_INVALID, "camera %d: look_at == pos", c); }
+        cross(F, up, R);
+        if (!normalize(R)) { delete sc; return fail(PT_E_INVALID, "camera %d: up parallel to view", c); }
+        cross(R, F, U);
+        DevCam& h = hc[c];
+        memset(&h, 0, sizeof(h));
+        for (int i = 0; i < 3; ++i) {
+            h.C[i] = k.pos[i]; h.F[i] = (float)F[i]; h.R[i] = (float)R[i]; h.U[i] = (float)U[i];
+        }
+        const double ty = std::tan(0.5 * (double)k.fov_y);
+        const double tx = ty * (double)k.width / (double)k.height;
+        tans[2 * c] = tx; tans[2 * c + 1] = ty;
+        h.inv_tx = (float)(1.0 / tx); h.inv_ty = (float)(1.0 / ty);
+        h.half_w = 0.5f * (float)k.width; h.half_h = 0.5f * (float)k.height;
+        h.W = k.width; h.H = k.height; h.off = (int)off;
+        off += (int64_t)k.width * k.height;
+    }
+    if (off >= ((int64_t)1 << 31)) { delete sc; return fail(PT_E_INVALID, "too many pixels"); }
+    sc->n_pixels = off;
+    S.n_pixels = off;
+    double* d_tans = nullptr;
+    int rc = PT_OK;
+    if ((rc = dev_alloc(&sc->d_cams, (uint64_t)d->n_cams, nullptr, "cameras")) ||
+        (rc = dev_alloc(&sc->d_omega, (uint64_t)off, nullptr, "pixel solid angles")) ||
+        (rc = dev_alloc(&sc->d_err, 1, nullptr, "error word")) ||
+        (rc = dev_alloc(&d_tans, (uint64_t)(2 * d->n_cams), nullptr, "tans"))) {
+        cudaFree(sc->d_cams); cudaFree(sc->d_omega); cudaFree(sc->d_err); cudaFree(d_tans);
+        delete sc;
+        return rc;
+    }
+    cudaError_t e = cudaMemcpy(sc->d_cams, hc, sizeof(DevCam) * d->n_cams, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_tans, tans, sizeof(double) * 2 * d->n_cams, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(sc->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        k_pixel_omega<<<(unsigned)((off + 255) / 256), 256>>>(sc->d_cams, d->n_cams, d_tans, sc->d_omega, off);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_tans);
+    if (e != cudaSuccess) {
+        cudaFree(sc->d_cams); cudaFree(sc->d_omega); cudaFree(sc->d_err);
+        delete sc;
+        return fail(PT_E_CUDA, "pt_scene_create: %s", cudaGetErrorString(e));
+    }
+    S.cams = sc->d_cams;
+    S.omega = sc->d_omega;
+    S.err = sc->d_err;
+    *out = sc;
+    return PT_OK;
+}
+
+int pt_scene_free(pt_scene* sc) {
+    if (!sc) return PT_OK;
+    cudaFree(sc->d_cams);
+    cudaFree(sc->d_omega);
+    cudaFree(sc->d_err);
+    delete sc;
+    return PT_OK;
+}
+
+int64_t pt_scene_pixels(const pt_scene* sc) { return sc ? sc->n_pixels : -1; }
+
+int render_forward(const pt_scene* sc, const float* beta, uint64_t first, uint64_t n, double n_norm, uint64_t seed,
+                   uint32_t epoch, double* images, uint32_t flags, double* tallies, uint64_t* fps, void* stream) {
+    if (!sc || !beta || !images) return fail(PT_E_INVALID, "render_forward: null scene, grid or images");
+    if (!(n_norm > 0.0)) return fail(PT_E_INVALID, "render_forward: n_norm must be > 0");
+    if (n >= ((uint64_t)1 << 40)) return fail(PT_E_INVALID, "render_forward: n_paths too large");
+    cudaStream_t st = S_(stream);
+    if (!(flags & PT_ACCUMULATE)) PT_CUDA(cudaMemsetAsync(images, 0, sizeof(double) * sc->n_pixels, st));
+    if (n == 0) return PT_OK;
+    launch_sample(sc->ds, beta, first, n, (float)(1.0 / n_norm), seed, epoch, images, tallies, fps, nullptr, st);
+    return launch_status("render_forward");
+}
+
+int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t n, double n_norm, uint64_t seed,
+                uint32_t epoch, pt_paths** pp, double* images_ref, uint32_t flags, double* tallies, uint64_t* fps,
+                void* stream) {
+    if (!sc || !beta || !pp) return fail(PT_E_INVALID, "paths_store: null scene, grid or handle slot");
+    if (!(n_norm > 0.0)) return fail(PT_E_INVALID, "paths_store: n_norm must be > 0");
+    if (n == 0 || n >= ((uint64_t)1 << 32)) return fail(PT_E_INVALID, "paths_store: n_paths must be in 1..2^32-1");
+    cudaStream_t st = S_(stream);
+    pt_paths* p = *pp;
+    bool created = false;
+    if (!p) {
+        p = new (std::nothrow) pt_paths();
+        if (!p) return fail(PT_E_OOM, "host allocation");
+        created = true;
+    } else if (p->scene != sc) {
+        return fail(PT_E_INVALID, "paths_store: handle belongs to another scene");
+    }
+    p->scene = sc;
+    const int slots = sc->ds.max_orders + 1;
+    if (p->cap < n || p->slots != slots) {
+        if (!created) PT_CUDA(cudaStreamSynchronize(st));
+        free_paths_buffers(p);
+        const uint64_t nblk = (n + 255) / 256;
+        int rc;
+        uint64_t by = 0;
+        p->V = sc->ds.V;
+        if ((rc = dev_alloc(&p->beta_ref, (uint64_t)p->V, &by, "beta_ref")) ||
+            (rc = dev_alloc(&p->dbeta, (uint64_t)p->V, &by, "dbeta")) ||
+            (rc = dev_alloc(&p->ua, n * slots, &by, "records A")) ||
+            (rc = dev_alloc(&p->ub, n * slots, &by, "records B")) ||
+            (rc = dev_alloc(&p->cnt, n, &by, "counts")) ||
+            (rc = dev_alloc(&p->sa, n * slots, &by, "sorted A")) ||
+            (rc = dev_alloc(&p->sb, n * slots, &by, "sorted B")) ||
+            (rc = dev_alloc(&p->blk, nblk * kBuckets, &by, "block histogram")) ||
+            (rc = dev_alloc(&p->bk, 1, &by, "buckets"))) {
+            free_paths_buffers(p);
+            if (created) delete p;
+            return rc;
+        }
+        p->cap = n;
+        p->slots = slots;
+        p->bytes = by;
+    }
+    p->n = n;
+    p->inv_norm = (float)(1.0 / n_norm);
+    p->cache_valid = false;
+    PT_CUDA(cudaMemcpyAsync(p->beta_ref, beta, sizeof(float) * p->V, cudaMemcpyDeviceToDevice, st));
+    if (images_ref && !(flags & PT_ACCUMULATE)) PT_CUDA(cudaMemsetAsync(images_ref, 0, sizeof(double) * sc->n_pixels, st));
+    StoreBuf sbuf{p->ua, p->ub, p->cnt, n};
+    // without images_ref the kernel traces flights only (no shadow rays)
+    launch_sample(sc->ds, beta, first, n, p->inv_norm, seed, epoch, images_ref, tallies, fps, &sbuf, st);
+    if (int rc = launch_status("paths_store")) return rc;
+    launch_sort(sbuf, n, slots, p->blk, p->bk, sc->ds.n_cams, p->sa, p->sb, st);
+    if (int rc = launch_status("paths_store sort")) return rc;
+    *pp = p;
+    return PT_OK;
+}
+
+int paths_reweight(pt_paths* p, const float* beta_t, double* images, uint32_t flags, void* stream) {
+    if (!p || !p->scene || !beta_t || !images) return fail(PT_E_INVALID, "paths_reweight: null argument");
+    if (p->n == 0) return fail(PT_E_INVALID, "paths_reweight: handle holds no paths");
+    cudaStream_t st = S_(stream);
+    const pt_scene* sc = p->scene;
+    float* cache = nullptr;
+    if (flags & PT_CACHE) {
+        const uint64_t need = p->n * (uint64_t)sc->ds.max_orders * (uint64_t)sc->ds.n_cams;
+        if (p->cache_cap < need) {
+            PT_CUDA(cudaStreamSynchronize(st));
+            cudaFree(p->cache);
+            p->cache = nullptr;
+            p->bytes -= p->cache_cap * sizeof(float);
+            p->cache_cap = 0;
+            if (int rc = dev_alloc(&p->cache, need, &p->bytes, "contribution cache")) return rc;
+            p->cache_cap = need;
+        }
+        cache = p->cache;
+    }
+    if (!(flags & PT_ACCUMULATE)) PT_CUDA(cudaMemsetAsync(images, 0, sizeof(double) * sc->n_pixels, st));
+    launch_delta(beta_t, p->beta_ref, p->dbeta, p->V, st);
+    launch_reweight(sc->ds, sorted_view(p), beta_t, p->beta_ref, p->dbeta, images, cache, st);
+    p->cache_valid = cache != nullptr;
+    return launch_status("paths_reweight");
+}
+
+int render_grad(pt_paths* p, const float* beta_t, const double* dldi, double* grad, uint32_t flags, void* stream) {
+    if (!p || !p->scene || !beta_t || !dldi || !grad) return fail(PT_E_INVALID, "render_grad: null argument");
+    if (p->n == 0) return fail(PT_E_INVALID, "render_grad: handle holds no paths");
+    if ((flags & PT_CACHE) && !p->cache_valid)
+        return fail(PT_E_INVALID, "render_grad: PT_CACHE without a preceding paths_reweight(PT_CACHE)");
+    cudaStream_t st = S_(stream);
+    const pt_scene* sc = p->scene;
+    if (!(flags & PT_ACCUMULATE)) PT_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * p->V, st));
+    if (!(flags & PT_CACHE)) launch_delta(beta_t, p->beta_ref, p->dbeta, p->V, st);
+    launch_grad(sc->ds, sorted_view(p), beta_t, p->beta_ref, p->dbeta, dldi, grad,
+                (flags & PT_CACHE) ? p->cache : nullptr, st);
+    return launch_status("render_grad");
+}
+
+int paths_free(pt_paths* p) {
+    if (!p) return PT_OK;
+    cudaDeviceSynchronize();
+    free_paths_buffers(p);
+    delete p;
+    return PT_OK;
+}
+
+int paths_info(const pt_paths* p, pt_paths_info* out, void* stream) {
+    if (!p || !out) return fail(PT_E_INVALID, "paths_info: null argument");
+    memset(out, 0, sizeof(*out));
+    out->n_paths = p->n;
+    out->bytes_device = p->bytes;
+    if (!p->bk || p->n == 0) return PT_OK;
+    Buckets h;
+    PT_CUDA(cudaMemcpyAsync(&h, p->bk, sizeof(h), cudaMemcpyDeviceToHost, S_(stream)));
+    PT_CUDA(cudaStreamSynchronize(S_(stream)));
+    for (int b = 0; b < kBuckets; ++b) out->bucket[b] = h.count[b];
+    out->n_stored = h.path_off[kBuckets];
+    out->n_records = h.rec_off[kBuckets];
+    return PT_OK;
+}
+
+int adam_step(float* beta, float* m, float* v, const double* grad, int64_t n, int32_t t, float lr, float b1, float b2,
+              float eps, void* stream) {
+    if (!beta || !m || !v || !grad || n < 0 || t < 1) return fail(PT_E_INVALID, "adam_step: bad argument");
+    if (n == 0) return PT_OK;
+    const double bc1 = 1.0 - std::pow((double)b1, (double)t);
+    const double bc2 = 1.0 - std::pow((double)b2, (double)t);
+    k_adam<<<grid_for(n, 256), 256, 0, S_(stream)>>>(beta, m, v, grad, n, lr, b1, b2, eps, (float)(1.0 / bc1),
+                                                      (float)(1.0 / bc2));
+    return launch_status("adam_step");
+}
+
+int loss_residual(const double* images, const double* gt, int64_t n, double* dldi, double* loss, void* stream) {
+    if (!images || !gt || !dldi || n < 0) return fail(PT_E_INVALID, "loss_residual: bad argument");
+    cudaStream_t st = S_(stream);
+    if (loss) PT_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), st));
+    if (n == 0) return PT_OK;
+    k_resid<<<grid_for(n, 256, 152 * 4), 256, 0, st>>>(images, gt, n, dldi, loss);
+    return launch_status("loss_residual");
+}
+
+int pt_check(const pt_scene* sc, void* stream) {
+    if (!sc) return fail(PT_E_INVALID, "pt_check: null scene");
+    int h = 0;
+    PT_CUDA(cudaMemcpyAsync(&h, sc->d_err, sizeof(int), cudaMemcpyDeviceToHost, S_(stream)));
+    PT_CUDA(cudaStreamSynchronize(S_(stream)));
+    if (h) {
+        PT_CUDA(cudaMemsetAsync(sc->d_err, 0, sizeof(int), S_(stream)));
+        PT_CUDA(cudaStreamSynchronize(S_(stream)));
+        return fail(PT_E_DEVICE_ASSERT, "kernel invariant violated (bits 0x%x: 1 index, 2 traversal length, 4 record)",
+                    h);
+    }
+    return PT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,280 @@
+"""Thin ctypes binding of libpathrecycle.so (C ABI in include/pathrecycle.h).
+
+Argument marshalling only: torch tensors provide device memory and the
+current CUDA stream; every step of the computation runs in the library's
+kernels.  There is no CPU fallback: if the library is missing or no GPU is
+present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import torch
+
+from . import build as _build
+
+PT_ACCUMULATE = 1
+PT_CACHE = 2
+TALLY_NAMES = ["injected", "missed", "escaped", "absorbed", "truncated", "rr_killed",
+               "rr_gain", "collisions", "entered", "seg_cross", "shadow_cross", "in_view"]
+TALLY_COUNT = len(TALLY_NAMES)
+MAX_ORDERS = 15
+
+_lib = None
+_lock = threading.Lock()
+
+
+class PtCamera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("look_at", C.c_float * 3), ("up", C.c_float * 3),
+                ("fov_y", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class PtSceneDesc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("voxel", C.c_float), ("origin", C.c_float * 3),
+                ("beta_air", C.c_float), ("albedo_cloud", C.c_float), ("albedo_air", C.c_float),
+                ("hg_g", C.c_float), ("sun_dir", C.c_float * 3), ("sun_irradiance", C.c_float),
+                ("n_cams", C.c_int32), ("cams", C.POINTER(PtCamera)),
+                ("max_orders", C.c_int32), ("rr_start", C.c_int32), ("rr_q", C.c_float),
+                ("scene_id", C.c_uint32)]
+
+
+class PtPathsInfo(C.Structure):
+    _fields_ = [("n_paths", C.c_uint64), ("n_stored", C.c_uint64), ("n_records", C.c_uint64),
+                ("bucket", C.c_uint64 * (MAX_ORDERS + 1)), ("bytes_device", C.c_uint64)]
+
+
+_vp = C.c_void_p
+_u64 = C.c_uint64
+_u32 = C.c_uint32
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libpathrecycle.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(path)
+        L.pt_scene_create.argtypes = [C.POINTER(PtSceneDesc), C.POINTER(_vp)]
+        L.pt_scene_free.argtypes = [_vp]
+        L.pt_scene_pixels.argtypes = [_vp]
+        L.pt_scene_pixels.restype = C.c_int64
+        L.render_forward.argtypes = [_vp, _vp, _u64, _u64, C.c_double, _u64, _u32, _vp, _u32, _vp, _vp, _vp]
+        L.paths_store.argtypes = [_vp, _vp, _u64, _u64, C.c_double, _u64, _u32, C.POINTER(_vp), _vp, _u32,
+                                  _vp, _vp, _vp]
+        L.paths_reweight.argtypes = [_vp, _vp, _vp, _u32, _vp]
+        L.render_grad.argtypes = [_vp, _vp, _vp, _vp, _u32, _vp]
+        L.paths_free.argtypes = [_vp]
+        L.paths_info.argtypes = [_vp, C.POINTER(PtPathsInfo), _vp]
+        L.adam_step.argtypes = [_vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.c_float, C.c_float, C.c_float,
+                                C.c_float, _vp]
+        L.loss_residual.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
+        L.pt_check.argtypes = [_vp, _vp]
+        L.pt_last_error.restype = C.c_char_p
+        L.pt_version.restype = C.c_char_p
+        _lib = L
+        return L
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        msg = load().pt_last_error().decode(errors="replace")
+        raise RuntimeError(f"{what} failed (status {rc}): {msg}")
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dev(t: torch.Tensor, dtype, what: str, numel: Optional[int] = None) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what}: expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{what}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: tensor must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{what}: expected {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+def _opt(t, dtype, what, numel=None):
+    return None if t is None else _dev(t, dtype, what, numel)
+
+
+class Scene:
+    """A scene on the current CUDA device (cameras, pixel solid angles, sun).
+
+    ``sc`` is any object with the attributes of a synthetic scene (grid
+    dims, voxel, medium constants, sun, cameras, termination settings).
+    """
+
+    def __init__(self, sc, scene_id: int = 0):
+        L = load()
+        cams = (PtCamera * len(sc.cameras))()
+        for i, c in enumerate(sc.cameras):
+            cams[i].pos[:] = [float(v) for v in c.pos]
+            cams[i].look_at[:] = [float(v) for v in c.look_at]
+            cams[i].up[:] = [float(v) for v in c.up]
+            cams[i].fov_y = float(c.fov_y)
+            cams[i].width = int(c.width)
+            cams[i].height = int(c.height)
+        d = PtSceneDesc()
+        d.nx, d.ny, d.nz = (int(k) for k in sc.n)
+        d.voxel = float(sc.voxel)
+        d.origin[:] = [float(v) for v in sc.origin]
+        d.beta_air = float(sc.beta_air)
+        d.albedo_cloud = float(sc.albedo_cloud)
+        d.albedo_air = float(sc.albedo_air)
+        d.hg_g = float(sc.hg_g)
+        d.sun_dir[:] = [float(v) for v in sc.sun_dir]
+        d.sun_irradiance = float(sc.sun_irradiance)
+        d.n_cams = len(sc.cameras)
+        d.cams = cams
+        d.max_orders = int(sc.max_orders)
+        d.rr_start = int(sc.rr_start)
+        d.rr_q = float(sc.rr_q)
+        d.scene_id = int(scene_id)
+        h = _vp()
+        _check(L.pt_scene_create(C.byref(d), C.byref(h)), "pt_scene_create")
+        self._h = h
+        self.spec = sc
+        self.n_pixels = int(L.pt_scene_pixels(h))
+        self.n_voxels = int(sc.n[0] * sc.n[1] * sc.n[2])
+        self.device = torch.cuda.current_device()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pt_scene_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def new_images(self) -> torch.Tensor:
+        return torch.zeros(self.n_pixels, dtype=torch.float64, device="cuda")
+
+    def check(self, stream=None):
+        _check(load().pt_check(self._h, _vp(_stream(stream))), "pt_check")
+
+    def render_forward(self, beta: torch.Tensor, n_paths: int, seed: int, first: int = 0, n_norm=None,
+                       epoch: int = 0, images: Optional[torch.Tensor] = None, accumulate: bool = False,
+                       tallies: Optional[torch.Tensor] = None, fingerprints: Optional[torch.Tensor] = None,
+                       stream=None) -> torch.Tensor:
+        if images is None:
+            images = self.new_images()
+        n_norm = float(n_paths if n_norm is None else n_norm)
+        rc = load().render_forward(self._h, _dev(beta, torch.float32, "beta", self.n_voxels), first, n_paths,
+                                   n_norm, seed, epoch, _dev(images, torch.float64, "images", self.n_pixels),
+                                   PT_ACCUMULATE if accumulate else 0,
+                                   _opt(tallies, torch.float64, "tallies", TALLY_COUNT),
+                                   _opt(fingerprints, torch.int64, "fingerprints", n_paths),
+                                   _vp(_stream(stream)))
+        _check(rc, "render_forward")
+        return images
+
+
+class Paths:
+    """Stored, size-sorted light paths (a ``pt_paths`` handle)."""
+
+    def __init__(self, scene: Scene):
+        self.scene = scene
+        self._h = _vp()
+
+    def store(self, beta: torch.Tensor, n_paths: int, seed: int, first: int = 0, n_norm=None, epoch: int = 0,
+              images_ref: Optional[torch.Tensor] = None, accumulate: bool = False,
+              tallies: Optional[torch.Tensor] = None, fingerprints: Optional[torch.Tensor] = None, stream=None):
+        n_norm = float(n_paths if n_norm is None else n_norm)
+        sc = self.scene
+        rc = load().paths_store(sc.handle, _dev(beta, torch.float32, "beta", sc.n_voxels), first, n_paths, n_norm,
+                                seed, epoch, C.byref(self._h),
+                                _opt(images_ref, torch.float64, "images_ref", sc.n_pixels),
+                                PT_ACCUMULATE if accumulate else 0,
+                                _opt(tallies, torch.float64, "tallies", TALLY_COUNT),
+                                _opt(fingerprints, torch.int64, "fingerprints", n_paths),
+                                _vp(_stream(stream)))
+        _check(rc, "paths_store")
+        return self
+
+    def reweight(self, beta_t: torch.Tensor, images: Optional[torch.Tensor] = None, cache: bool = False,
+                 accumulate: bool = False, stream=None) -> torch.Tensor:
+        sc = self.scene
+        if images is None:
+            images = sc.new_images()
+        flags = (PT_CACHE if cache else 0) | (PT_ACCUMULATE if accumulate else 0)
+        rc = load().paths_reweight(self._h, _dev(beta_t, torch.float32, "beta_t", sc.n_voxels),
+                                   _dev(images, torch.float64, "images", sc.n_pixels), flags,
+                                   _vp(_stream(stream)))
+        _check(rc, "paths_reweight")
+        return images
+
+    def grad(self, beta_t: torch.Tensor, dldi: torch.Tensor, grad: Optional[torch.Tensor] = None,
+             cache: bool = False, accumulate: bool = False, stream=None) -> torch.Tensor:
+        sc = self.scene
+        if grad is None:
+            grad = torch.zeros(sc.n_voxels, dtype=torch.float64, device="cuda")
+        flags = (PT_CACHE if cache else 0) | (PT_ACCUMULATE if accumulate else 0)
+        rc = load().render_grad(self._h, _dev(beta_t, torch.float32, "beta_t", sc.n_voxels),
+                                _dev(dldi, torch.float64, "dL_dI", sc.n_pixels),
+                                _dev(grad, torch.float64, "grad", sc.n_voxels), flags, _vp(_stream(stream)))
+        _check(rc, "render_grad")
+        return grad
+
+    def info(self, stream=None) -> dict:
+        inf = PtPathsInfo()
+        _check(load().paths_info(self._h, C.byref(inf), _vp(_stream(stream))), "paths_info")
+        return {"n_paths": inf.n_paths, "n_stored": inf.n_stored, "n_records": inf.n_records,
+                "bucket": list(inf.bucket), "bytes_device": inf.bytes_device}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().paths_free(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def adam_step(beta, m, v, grad, t: int, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8,
+              stream=None):
+    n = beta.numel()
+    rc = load().adam_step(_dev(beta, torch.float32, "beta"), _dev(m, torch.float32, "m", n),
+                          _dev(v, torch.float32, "v", n), _dev(grad, torch.float64, "grad", n), n, int(t),
+                          float(lr), float(b1), float(b2), float(eps), _vp(_stream(stream)))
+    _check(rc, "adam_step")
+
+
+def loss_residual(images, gt, dldi=None, loss=None, stream=None):
+    n = images.numel()
+    if dldi is None:
+        dldi = torch.empty_like(images)
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float64, device=images.device)
+    rc = load().loss_residual(_dev(images, torch.float64, "images"), _dev(gt, torch.float64, "gt", n), n,
+                              _dev(dldi, torch.float64, "dL_dI", n), _dev(loss, torch.float64, "loss", 1),
+                              _vp(_stream(stream)))
+    _check(rc, "loss_residual")
+    return dldi, loss

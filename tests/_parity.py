@@ -1,0 +1,125 @@
+"""Helpers for comparing the CUDA path with the oracle on identical Philox
+streams.
+
+FP32 path arithmetic on the GPU and FP64 in the oracle take the same discrete
+decisions (collision voxel, escape, roulette, particle type, pixel) except for
+rare near-ties.  Both sides emit a per-path fingerprint of those decisions;
+the paths whose fingerprints differ are rendered one by one on each side
+(same path id, same normalisation) and removed from both totals before the
+element-wise comparison.  No value computed by the CUDA path enters the
+oracle: only the list of path ids to leave out is shared.
+"""
+import numpy as np
+import torch
+
+import oracle as O
+from paper_2110_00085_gb300 import native as N
+
+RTOL = 1e-4          # per pixel, per voxel (of the voxel's absolute term mass)
+MAX_DIVERGENT = 2e-3  # fraction of paths whose discrete decisions may differ
+U32 = 2.0 ** -24      # FP32 unit roundoff
+
+
+def t32(a):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, np.float32).reshape(-1))).cuda()
+
+
+def t64(a):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, np.float64).reshape(-1))).cuda()
+
+
+def divergent(fp_gpu: torch.Tensor, fp_oracle: np.ndarray, first: int = 0):
+    g = fp_gpu.cpu().numpy().view(np.uint64)
+    return np.nonzero(g != fp_oracle)[0] + first
+
+
+def assert_images_close(gi, oi, rtol=RTOL, what="images"):
+    gi = np.asarray(gi)
+    oi = np.asarray(oi)
+    atol = 1e-9 * max(np.abs(oi).max(), 1e-300)
+    err = np.abs(gi - oi)
+    bad = err > rtol * np.abs(oi) + atol
+    if bad.any():
+        k = np.argmax(err / (np.abs(oi) + atol))
+        raise AssertionError(f"{what}: {bad.sum()} of {bad.size} elements off; worst at {k}: "
+                             f"gpu {gi[k]:.9e} oracle {oi[k]:.9e}")
+
+
+def assert_grad_close(gg, og, oabs, ocond=None, rtol=RTOL, what="grad"):
+    """Per voxel: |g_gpu - g_oracle| <= rtol * sum|terms| + cond.
+    cond (the oracle's float32 error budget) sums, over the voxel's length
+    terms, |coefficient| * (1/|d_axis| of each face bounding the crossing) *
+    (float32 position uncertainty of the ray's origin vertex): a crossing's
+    position along a ray moves by (normal displacement) / |d_axis|."""
+    gg = np.asarray(gg)
+    err = np.abs(gg - og)
+    floor = 1e-12 * max(oabs.max(), 1e-300)
+    if ocond is not None:
+        floor = floor + ocond
+    bad = err > rtol * oabs + floor
+    if bad.any():
+        budget = rtol * oabs + floor
+        k = np.argmax(err / budget)
+        raise AssertionError(f"{what}: {bad.sum()} of {bad.size} voxels off; worst at {k}: gpu {gg[k]:.9e} "
+                             f"oracle {og[k]:.9e} |terms| {oabs[k]:.3e} budget {budget[k]:.3e}")
+
+
+def forward_parity(sc, beta, n, first=0, seed=None):
+    """Returns (gpu images, oracle images) with divergent paths removed."""
+    seed = sc.seed if seed is None else seed
+    scene = N.Scene(sc)
+    b = t32(beta)
+    fp = torch.zeros(n, dtype=torch.int64, device="cuda")
+    tal = torch.zeros(N.TALLY_COUNT, dtype=torch.float64, device="cuda")
+    img = scene.render_forward(b, n, seed, first=first, tallies=tal, fingerprints=fp)
+    ref = O.render(sc, beta, first=first, n=n, seed=seed, fingerprints=True, tallies=True)
+    div = divergent(fp, ref["fingerprints"], first)
+    assert len(div) <= max(3, MAX_DIVERGENT * n), f"{len(div)} divergent paths of {n}"
+    gi = img.clone()
+    oi = ref["images"].copy()
+    for p in div:
+        e = scene.render_forward(b, 1, seed, first=int(p), n_norm=n)
+        gi -= e
+        oi -= O.render(sc, beta, first=int(p), n=1, n_norm=n, seed=seed)["images"]
+    torch.cuda.synchronize()
+    scene.check()
+    return gi.cpu().numpy(), oi, tal.cpu().numpy(), ref["tallies"], len(div)
+
+
+def recycled_parity(sc, beta_ref, beta_t, n, dldi=None, cache=False, first=0):
+    """Paths stored under beta_ref, evaluated under beta_t, on both sides.
+    Returns dict of gpu/oracle images (and gradients), divergent removed."""
+    scene = N.Scene(sc)
+    br, bt = t32(beta_ref), t32(beta_t)
+    fp = torch.zeros(n, dtype=torch.int64, device="cuda")
+    paths = N.Paths(scene).store(br, n, sc.seed, first=first, fingerprints=fp)
+    img = paths.reweight(bt, cache=cache)
+    ref = O.render(sc, beta_ref, beta_t, first=first, n=n, fingerprints=True,
+                   dldi=dldi, grad_abs=dldi is not None, grad_cond=dldi is not None)
+    out = {"gpu_images": img, "oracle_images": ref["images"].copy()}
+    if dldi is not None:
+        g = paths.grad(bt, t64(dldi), cache=cache)
+        out["gpu_grad"] = g
+        out["oracle_grad"] = ref["grad"].copy()
+        out["oracle_grad_abs"] = ref["grad_abs"]
+        out["oracle_grad_cond"] = ref["grad_cond"]
+    div = divergent(fp, ref["fingerprints"], first)
+    assert len(div) <= max(3, MAX_DIVERGENT * n), f"{len(div)} divergent paths of {n}"
+    for p in div:
+        one = N.Paths(scene).store(br, 1, sc.seed, first=int(p), n_norm=n)
+        out["gpu_images"] -= one.reweight(bt)
+        r1 = O.render(sc, beta_ref, beta_t, first=int(p), n=1, n_norm=n, dldi=dldi)
+        out["oracle_images"] -= r1["images"]
+        if dldi is not None:
+            out["gpu_grad"] -= one.grad(bt, t64(dldi))
+            out["oracle_grad"] -= r1["grad"]
+        one.close()
+    torch.cuda.synchronize()
+    scene.check()
+    out["gpu_images"] = out["gpu_images"].cpu().numpy()
+    if dldi is not None:
+        out["gpu_grad"] = out["gpu_grad"].cpu().numpy()
+    out["divergent"] = len(div)
+    out["paths"] = paths
+    out["scene"] = scene
+    return out

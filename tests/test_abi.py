@@ -1,0 +1,79 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for
+sm_103a, loads, and exports every entry point include/pathrecycle.h declares;
+the binding refuses what it cannot run."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pathrecycle.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "sizeof")))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("render_forward", "render_grad", "paths_store", "paths_reweight", "paths_free",
+              "pt_last_error", "pt_scene_create", "adam_step", "loss_residual"):
+        assert n in names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    from paper_2110_00085_gb300 import build as B
+    path = B.build()
+    lib = C.CDLL(path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    lib.pt_version.restype = C.c_char_p
+    assert b"sm_103a" in lib.pt_version()
+
+
+def test_null_arguments_are_rejected_without_a_gpu():
+    from paper_2110_00085_gb300 import native as N
+    L = N.load()
+    assert L.render_forward(None, None, 0, 0, 1.0, 0, 0, None, 0, None, None, None) == 1
+    assert b"null" in L.pt_last_error()
+    assert L.pt_scene_create(None, None) == 1
+    assert L.paths_reweight(None, None, None, 0, None) == 1
+    assert L.render_grad(None, None, None, None, 0, None) == 1
+    assert L.adam_step(None, None, None, None, 0, 0, 0.0, 0.0, 0.0, 0.0, None) == 1
+
+
+def test_scene_descriptor_validation_runs_on_host():
+    from paper_2110_00085_gb300 import native as N
+    L = N.load()
+    d = N.PtSceneDesc()
+    d.nx = d.ny = d.nz = 4
+    d.voxel = 0.0
+    h = C.c_void_p()
+    assert L.pt_scene_create(C.byref(d), C.byref(h)) == 1
+    assert b"voxel" in L.pt_last_error()
+    d.voxel = 0.02
+    d.n_cams = 0
+    assert L.pt_scene_create(C.byref(d), C.byref(h)) == 1
+    assert b"n_cams" in L.pt_last_error()
+
+
+def test_binding_has_no_cpu_fallback():
+    """The binding only marshals device tensors; CPU tensors are refused."""
+    import torch
+    from paper_2110_00085_gb300 import native as N
+    with pytest.raises(TypeError):
+        N._dev(torch.zeros(4), torch.float32, "beta")
+
+
+def test_oracle_is_not_imported_by_the_package():
+    pkg = os.path.join(ROOT, "paper_2110_00085_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "oracle.c" not in txt, f

@@ -1,0 +1,192 @@
+"""CUDA path vs. the FP64 oracle, element by element, on identical Philox
+streams (relative 1e-4 per pixel and per voxel), plus the invariants that
+hold at any size.  Needs a GB300."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2110_00085_gb300 import native as N
+from paper_2110_00085_gb300 import synth
+
+from _parity import (RTOL, assert_grad_close, assert_images_close, forward_parity, recycled_parity, t32, t64)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    torch.cuda.set_device(0)
+
+
+def _perturbed(beta, seed=0, lo=0.85, hi=1.2):
+    rng = np.random.default_rng(seed)
+    return (beta * rng.uniform(lo, hi, size=beta.shape)).astype(np.float32)
+
+
+# ------------------------------------------------------------ forward ------
+@pytest.mark.parametrize("cfg,n,first", [(1, 1 << 14, 0), (1, 5000, 123457), (2, 1 << 11, 0)])
+def test_forward_matches_oracle(cfg, n, first):
+    """Plain path tracing (Alg. 1 forward): 2^14 paths (many tiles) and a
+    ragged count at an offset path id; workload 2 has air (two types)."""
+    sc = synth.config(cfg, n_paths=n)
+    gi, oi, tg, to, nd = forward_parity(sc, sc.beta_cloud, n, first=first)
+    assert np.abs(oi).max() > 0
+    assert_images_close(gi, oi)
+    # tallies: collision and path counts are integers; weights FP32-summed
+    names = N.TALLY_NAMES
+    for k in ("entered", "collisions"):
+        assert abs(tg[names.index(k)] - to[k]) <= 2 * nd + 1
+    for k in ("injected", "escaped", "absorbed"):
+        assert abs(tg[names.index(k)] - to[k]) <= 1e-3 * to["injected"]
+
+
+def test_energy_balance_on_gpu():
+    sc = synth.config(1, n_paths=1 << 16)
+    scene = N.Scene(sc)
+    tal = torch.zeros(N.TALLY_COUNT, dtype=torch.float64, device="cuda")
+    scene.render_forward(t32(sc.beta_cloud), sc.n_paths, sc.seed, tallies=tal)
+    T = dict(zip(N.TALLY_NAMES, tal.cpu().numpy()))
+    lhs = T["injected"] + T["rr_gain"]
+    rhs = T["escaped"] + T["absorbed"] + T["truncated"] + T["rr_killed"]
+    assert abs(lhs - rhs) < 1e-5 * lhs
+
+
+def test_forward_chunks_add_up():
+    """Two calls over disjoint path ranges accumulate to the one-call image."""
+    sc = synth.config(1, n_paths=1 << 13)
+    scene = N.Scene(sc)
+    b = t32(sc.beta_cloud)
+    n = sc.n_paths
+    full = scene.render_forward(b, n, sc.seed)
+    part = scene.render_forward(b, 3000, sc.seed, n_norm=n)
+    scene.render_forward(b, n - 3000, sc.seed, first=3000, n_norm=n, images=part, accumulate=True)
+    assert torch.allclose(full, part, rtol=1e-12, atol=0)
+
+
+# ------------------------------------------------------------ recycling ---
+@pytest.mark.parametrize("cfg,n", [(1, 1 << 14), (2, 1 << 11)])
+def test_recycled_forward_matches_oracle(cfg, n):
+    """Paths stored under M_ref, reweighted to M_t (Eq. 19/20)."""
+    sc = synth.config(cfg, n_paths=n)
+    bt = _perturbed(sc.beta_cloud, seed=cfg)
+    out = recycled_parity(sc, sc.beta_cloud, bt, n)
+    assert_images_close(out["gpu_images"], out["oracle_images"], what="recycled images")
+
+
+def test_recycling_ratio_is_one_at_reference():
+    """r == 1 when M_t == M_ref: the recycled pass reproduces the store's own
+    plain estimate (same contributions, only the FP64 summation order differs)."""
+    sc = synth.config(1, n_paths=1 << 15)
+    scene = N.Scene(sc)
+    b = t32(sc.beta_cloud)
+    ref = scene.new_images()
+    paths = N.Paths(scene).store(b, sc.n_paths, sc.seed, images_ref=ref)
+    again = paths.reweight(b.clone())
+    plain = scene.render_forward(b, sc.n_paths, sc.seed)
+    assert torch.allclose(again, ref, rtol=1e-11, atol=0)
+    assert torch.allclose(plain, ref, rtol=1e-11, atol=0)
+
+
+def test_sorted_buckets_are_consistent():
+    """Counting sort: bucket sizes add up to the stored paths, and sum B*count
+    equals the collision tally."""
+    sc = synth.config(1, n_paths=1 << 15)
+    scene = N.Scene(sc)
+    b = t32(sc.beta_cloud)
+    tal = torch.zeros(N.TALLY_COUNT, dtype=torch.float64, device="cuda")
+    paths = N.Paths(scene).store(b, sc.n_paths, sc.seed, tallies=tal)
+    info = paths.info()
+    T = dict(zip(N.TALLY_NAMES, tal.cpu().numpy()))
+    bk = info["bucket"]
+    assert sum(bk[1:]) == info["n_stored"]
+    assert sum(k * c for k, c in enumerate(bk)) == int(T["collisions"])
+    assert sum(bk) == int(T["entered"])
+    assert info["n_records"] == sum((k + 1) * c for k, c in enumerate(bk) if k >= 1)
+
+
+# ------------------------------------------------------------ gradient -----
+@pytest.mark.parametrize("cfg,n,cache", [(1, 1 << 13, False), (1, 1 << 13, True), (2, 1 << 10, True)])
+def test_gradient_matches_oracle(cfg, n, cache):
+    """render_grad (Eq. 21 with the PSF of Sec. 4.4) vs. the oracle's
+    term-by-term gradient, per voxel, relative to the voxel's term mass."""
+    sc = synth.config(cfg, n_paths=n)
+    bt = _perturbed(sc.beta_cloud, seed=10 + cfg)
+    gt = 0.8 * O.render(sc, sc.beta_cloud, n=n, seed=sc.seed + 99)["images"]
+    F = O.render(sc, sc.beta_cloud, bt, n=n)["images"]
+    dldi = F - gt
+    out = recycled_parity(sc, sc.beta_cloud, bt, n, dldi=dldi, cache=cache)
+    assert np.abs(out["oracle_grad"]).max() > 0
+    assert_grad_close(out["gpu_grad"], out["oracle_grad"], out["oracle_grad_abs"], out["oracle_grad_cond"])
+
+
+def test_gradient_cache_equals_recompute():
+    sc = synth.config(1, n_paths=1 << 14)
+    scene = N.Scene(sc)
+    br, bt = t32(sc.beta_cloud), t32(_perturbed(sc.beta_cloud, 5))
+    paths = N.Paths(scene).store(br, sc.n_paths, sc.seed)
+    img = paths.reweight(bt, cache=True)
+    dldi = img - 0.5 * img.mean()
+    g1 = paths.grad(bt, dldi, cache=True)
+    g2 = paths.grad(bt, dldi, cache=False)
+    assert torch.allclose(g1, g2, rtol=1e-6, atol=1e-9 * g2.abs().max().item())
+
+
+# ------------------------------------------------------------ edge cases ---
+def test_empty_medium_gives_zero():
+    sc = synth.config(1, n_paths=1 << 10)
+    scene = N.Scene(sc)
+    z = torch.zeros(sc.n_voxels, dtype=torch.float32, device="cuda")
+    img = scene.render_forward(z, sc.n_paths, sc.seed)
+    assert img.abs().max().item() == 0.0
+    paths = N.Paths(scene).store(z, sc.n_paths, sc.seed)
+    assert paths.info()["n_stored"] == 0
+    assert paths.reweight(z).abs().max().item() == 0.0
+    g = paths.grad(z, torch.ones(scene.n_pixels, dtype=torch.float64, device="cuda"))
+    assert g.abs().max().item() == 0.0
+
+
+def test_single_path_and_first_order_only():
+    sc = synth.config(1, n_paths=1).replace(max_orders=1)
+    gi, oi, *_ = forward_parity(sc, sc.beta_cloud, 64, first=777)
+    assert_images_close(gi, oi)
+
+
+def test_invalid_arguments_raise():
+    sc = synth.config(1, n_paths=16)
+    scene = N.Scene(sc)
+    with pytest.raises(ValueError):
+        scene.render_forward(torch.zeros(5, device="cuda"), 16, 1)
+    bad = sc.replace(max_orders=99)
+    with pytest.raises(RuntimeError):
+        N.Scene(bad)
+    p = N.Paths(scene)
+    with pytest.raises(RuntimeError):
+        p.reweight(t32(sc.beta_cloud))
+
+
+# ------------------------------------------------------------ loss, Adam ---
+def test_loss_residual_and_adam_match_reference():
+    rng = np.random.default_rng(3)
+    img = rng.normal(size=1000)
+    gt = rng.normal(size=1000)
+    d, loss = N.loss_residual(t64(img), t64(gt))
+    assert np.allclose(d.cpu().numpy(), img - gt, rtol=0, atol=0)
+    assert abs(loss.item() - 0.5 * np.sum((img - gt) ** 2)) < 1e-12 * np.sum((img - gt) ** 2)
+    beta = rng.uniform(0, 5, size=4096).astype(np.float32)
+    g = rng.normal(size=4096) * 1e-3
+    m = np.zeros(4096, np.float32)
+    v = np.zeros(4096, np.float32)
+    tb, tm, tv = t32(beta), t32(m), t32(v)
+    rb, rm, rv = beta.astype(np.float64), m.astype(np.float64), v.astype(np.float64)
+    for t in range(1, 6):
+        N.adam_step(tb, tm, tv, t64(g * t), t, lr=0.1)
+        rb, rm, rv = O.adam_step(rb, rm, rv, g * t, t, lr=0.1)
+    assert np.allclose(tb.cpu().numpy(), rb, rtol=1e-5, atol=1e-5)
+    assert (tb.cpu().numpy() >= 0).all()

@@ -143,10 +143,10 @@ def test_camera_frame():
     for i, cam in enumerate(sc.cameras):
         f = O.camera_frame(sc, i)
         fwd = np.subtract(cam.look_at, cam.pos); fwd /= np.linalg.norm(fwd)
-        assert np.allclose(f["F"], fwd)
+        assert np.allclose(f["F"], fwd, atol=1e-6)
         assert abs(f["R"] @ f["F"]) < 1e-12 and abs(f["U"] @ f["F"]) < 1e-12
         assert f["U"] @ np.array(cam.up) > 0
-        assert abs(f["ty"] - math.tan(cam.fov_y / 2)) < 1e-12
+        assert abs(f["ty"] - math.tan(float(np.float32(cam.fov_y)) / 2)) < 1e-12
 
 
 # --------------------------------------------------- grid traversal (DDA) ---
