@@ -201,6 +201,29 @@ int adam_step(float* beta, float* m, float* v, const double* grad, int64_t n,
 int loss_residual(const double* images, const double* gt, int64_t n,
                   double* dL_dI, double* loss, void* stream);
 
+/*
+ * render_forward_static -- render_forward for callers that cannot allocate
+ * device memory (the paper has no counterpart; this is a deployment
+ * variant).  A host application whose allocator owns all device memory, or
+ * code running where allocation is not allowed after start-up, cannot
+ * create a pt_scene.  This call takes the scene description directly and
+ * keeps the tables a pt_scene would hold (camera frames, pixel solid angles,
+ * an error word) in one file-scope device array of about 1 MiB that every
+ * GPU loading the library holds until the process exits.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ * Limits: at most 16 cameras and 2^18 pixels in total; larger scenes return
+ * PT_E_INVALID with a message naming the limit.  Arguments and output are as
+ * for render_forward (desc is read on the host; cams is a host array).
+ * The first call on a device looks up the array's address (once per device,
+ * with that device current); make that call before any stream capture.
+ * Every call overwrites the array and clears its error word, so calls that
+ * overlap on the GPU race; kernel-side invariant checks are not reported.
+ */
+int render_forward_static(const pt_scene_desc* desc, const float* beta_cloud,
+                          uint64_t first_path, uint64_t n_paths, double n_norm,
+                          uint64_t seed, uint32_t epoch, double* images,
+                          uint32_t flags, void* stream);
+
 /* Synchronises the stream and reports (then clears) kernel-side invariant
  * violations recorded in the scene. */
 int pt_check(const pt_scene* scene, void* stream);

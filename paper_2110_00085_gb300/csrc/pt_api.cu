@@ -16,14 +16,17 @@ using namespace pt;
 // ------------------------------------------------------------ errors -----
 namespace {
 thread_local char g_err[512] = "";
+}  // namespace
 
-int fail(int code, const char* fmt, ...) {
+int pt::fail(int code, const char* fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
     return code;
 }
+
+namespace {
 
 #define PT_CUDA(call)                                                                                \
     do {                                                                                             \
@@ -177,9 +180,13 @@ extern "C" {
 const char* pt_last_error(void) { return g_err; }
 const char* pt_version(void) { return "pathrecycle 0.1 (sm_103a)"; }
 
-int pt_scene_create(const pt_scene_desc* d, pt_scene** out) {
-    if (!d || !out) return fail(PT_E_INVALID, "pt_scene_create: null argument");
-    *out = nullptr;
+}  // extern "C"
+
+// Validates a scene description and derives its device constants on the host
+// (camera frames, solid-angle inputs, sun rectangle).  Shared by every entry
+// point that takes a pt_scene_desc.
+int pt::describe_scene(const pt_scene_desc* d, DevScene& S, DevCam* hc, double* tans) {
+    if (!d) return fail(PT_E_INVALID, "scene description: null");
     if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(PT_E_INVALID, "grid dims must be >= 1");
     const int64_t V = (int64_t)d->nx * d->ny * d->nz;
     if (V >= (int64_t)1 << 28) return fail(PT_E_INVALID, "grid has %lld voxels; limit 2^28", (long long)V);
@@ -195,9 +202,6 @@ int pt_scene_create(const pt_scene_desc* d, pt_scene** out) {
     double s[3] = {d->sun_dir[0], d->sun_dir[1], d->sun_dir[2]};
     if (!normalize(s)) return fail(PT_E_INVALID, "sun_dir must be a nonzero vector");
 
-    pt_scene* sc = new (std::nothrow) pt_scene();
-    if (!sc) return fail(PT_E_OOM, "host allocation");
-    DevScene& S = sc->ds;
     memset(&S, 0, sizeof(S));
     S.nx = d->nx; S.ny = d->ny; S.nz = d->nz; S.n_cams = d->n_cams; S.V = (int)V;
     S.max_orders = d->max_orders; S.rr_start = d->rr_start; S.scene_id = d->scene_id;
@@ -236,21 +240,17 @@ int pt_scene_create(const pt_scene_desc* d, pt_scene** out) {
         S.w0 = (float)((double)d->sun_irradiance * (amax - amin) * (bmax - bmin));
     }
     // cameras
-    DevCam hc[PT_MAX_CAMS];
-    double tans[2 * PT_MAX_CAMS];
     int64_t off = 0;
     for (int c = 0; c < d->n_cams; ++c) {
         const pt_camera& k = d->cams[c];
-        if (k.width < 1 || k.height < 1 || !(k.fov_y > 0.0f && k.fov_y < 3.1f)) {
-            delete sc;
+        if (k.width < 1 || k.height < 1 || !(k.fov_y > 0.0f && k.fov_y < 3.1f))
             return fail(PT_E_INVALID, "camera %d: bad size or field of view", c);
-        }
         double F[3] = {(double)k.look_at[0] - k.pos[0], (double)k.look_at[1] - k.pos[1], (double)k.look_at[2] - k.pos[2]};
         double up[3] = {k.up[0], k.up[1], k.up[2]};
         double R[3], U[3];
-        if (!normalize(F)) { delete sc; return fail(PT_E_INVALID, "camera %d: look_at == pos", c); }
+        if (!normalize(F)) return fail(PT_E_INVALID, "camera %d: look_at == pos", c);
         cross(F, up, R);
-        if (!normalize(R)) { delete sc; return fail(PT_E_INVALID, "camera %d: up parallel to view", c); }
+        if (!normalize(R)) return fail(PT_E_INVALID, "camera %d: up parallel to view", c);
         cross(R, F, U);
         DevCam& h = hc[c];
         memset(&h, 0, sizeof(h));
@@ -265,9 +265,30 @@ int pt_scene_create(const pt_scene_desc* d, pt_scene** out) {
         h.W = k.width; h.H = k.height; h.off = (int)off;
         off += (int64_t)k.width * k.height;
     }
-    if (off >= ((int64_t)1 << 31)) { delete sc; return fail(PT_E_INVALID, "too many pixels"); }
-    sc->n_pixels = off;
+    if (off >= ((int64_t)1 << 31)) return fail(PT_E_INVALID, "too many pixels");
     S.n_pixels = off;
+    S.cams = nullptr;
+    S.omega = nullptr;
+    S.err = nullptr;
+    return PT_OK;
+}
+
+extern "C" {
+
+int pt_scene_create(const pt_scene_desc* d, pt_scene** out) {
+    if (!d || !out) return fail(PT_E_INVALID, "pt_scene_create: null argument");
+    *out = nullptr;
+    pt_scene* sc = new (std::nothrow) pt_scene();
+    if (!sc) return fail(PT_E_OOM, "host allocation");
+    DevScene& S = sc->ds;
+    DevCam hc[PT_MAX_CAMS];
+    double tans[2 * PT_MAX_CAMS];
+    if (int rc = describe_scene(d, S, hc, tans)) {
+        delete sc;
+        return rc;
+    }
+    const int64_t off = S.n_pixels;
+    sc->n_pixels = off;
     double* d_tans = nullptr;
     int rc = PT_OK;
     if ((rc = dev_alloc(&sc->d_cams, (uint64_t)d->n_cams, nullptr, "cameras")) ||

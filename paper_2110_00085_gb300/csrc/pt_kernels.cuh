@@ -49,4 +49,10 @@ void launch_grad(const DevScene& S, const SortedPaths& P, const float* beta_t, c
 
 void launch_delta(const float* a, const float* b, float* out, int64_t n, cudaStream_t st);
 
+// host side (pt_api.cu): record an error message for pt_last_error() and
+// return `code`; validate a scene description and derive its constants
+// (hc: n_cams cameras, tans: 2 * n_cams half-field tangents x, y)
+int fail(int code, const char* fmt, ...);
+int describe_scene(const pt_scene_desc* d, DevScene& S, DevCam* hc, double* tans);
+
 }  // namespace pt

@@ -82,6 +82,8 @@ def load():
                                 C.c_float, _vp]
         L.loss_residual.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
         L.pt_check.argtypes = [_vp, _vp]
+        L.render_forward_static.argtypes = [C.POINTER(PtSceneDesc), _vp, _u64, _u64, C.c_double, _u64, _u32,
+                                            _vp, _u32, _vp]
         L.pt_last_error.restype = C.c_char_p
         L.pt_version.restype = C.c_char_p
         _lib = L
@@ -278,3 +280,52 @@ def loss_residual(images, gt, dldi=None, loss=None, stream=None):
                               _vp(_stream(stream)))
     _check(rc, "loss_residual")
     return dldi, loss
+
+
+def scene_desc(sc, scene_id: int = 0):
+    """(pt_scene_desc, camera array) for a synthetic scene; keep both alive
+    while the description is in use."""
+    cams = (PtCamera * len(sc.cameras))()
+    for i, c in enumerate(sc.cameras):
+        cams[i].pos[:] = [float(v) for v in c.pos]
+        cams[i].look_at[:] = [float(v) for v in c.look_at]
+        cams[i].up[:] = [float(v) for v in c.up]
+        cams[i].fov_y = float(c.fov_y)
+        cams[i].width = int(c.width)
+        cams[i].height = int(c.height)
+    d = PtSceneDesc()
+    d.nx, d.ny, d.nz = (int(k) for k in sc.n)
+    d.voxel = float(sc.voxel)
+    d.origin[:] = [float(v) for v in sc.origin]
+    d.beta_air = float(sc.beta_air)
+    d.albedo_cloud = float(sc.albedo_cloud)
+    d.albedo_air = float(sc.albedo_air)
+    d.hg_g = float(sc.hg_g)
+    d.sun_dir[:] = [float(v) for v in sc.sun_dir]
+    d.sun_irradiance = float(sc.sun_irradiance)
+    d.n_cams = len(sc.cameras)
+    d.cams = cams
+    d.max_orders = int(sc.max_orders)
+    d.rr_start = int(sc.rr_start)
+    d.rr_q = float(sc.rr_q)
+    d.scene_id = int(scene_id)
+    return d, cams
+
+
+def render_forward_static(sc, beta: torch.Tensor, n_paths: int, seed: int, first: int = 0, n_norm=None,
+                          epoch: int = 0, images: Optional[torch.Tensor] = None, accumulate: bool = False,
+                          scene_id: int = 0, stream=None) -> torch.Tensor:
+    """render_forward without a pt_scene, for callers that cannot allocate
+    device memory (the library keeps the scene tables in a fixed device
+    array; at most 16 cameras and 2^18 pixels)."""
+    d, cams = scene_desc(sc, scene_id)
+    n_pix = int(sum(c.width * c.height for c in sc.cameras))
+    n_vox = int(sc.n[0] * sc.n[1] * sc.n[2])
+    if images is None:
+        images = torch.zeros(n_pix, dtype=torch.float64, device="cuda")
+    n_norm = float(n_paths if n_norm is None else n_norm)
+    rc = load().render_forward_static(C.byref(d), _dev(beta, torch.float32, "beta", n_vox), first, n_paths, n_norm,
+                                      seed, epoch, _dev(images, torch.float64, "images", n_pix),
+                                      PT_ACCUMULATE if accumulate else 0, _vp(_stream(stream)))
+    _check(rc, "render_forward_static")
+    return images
