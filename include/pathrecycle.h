@@ -17,7 +17,7 @@
  *
  * Conventions shared by every call
  *   - Units: km and 1/km.  Grids are float32, x fastest (index
- *     x + nx*(y + ny*z)), nx*ny*nz < 2^28.
+ *     x + nx*(y + ny*z)), at most 512 voxels per axis.
  *   - Images are float64, camera after camera, each row-major W x H with
  *     row 0 at the top; pixel values are radiance averaged over the pixel's
  *     solid angle, for unit sun irradiance times sun_irradiance.

@@ -3,6 +3,7 @@
 // element-wise kernels (pixel solid angles, grid difference, loss residual,
 // Adam).  Every call launches on the caller's stream; errors are returned,
 // never raised, and described by pt_last_error().
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -137,6 +138,7 @@ struct pt_paths {
     float4* sb = nullptr;
     uint32_t* blk = nullptr;
     Buckets* bk = nullptr;
+    Events ev{};
     float* cache = nullptr;
     uint64_t cache_cap = 0;    // floats
     uint64_t bytes = 0;
@@ -147,8 +149,19 @@ namespace {
 void free_paths_buffers(pt_paths* p) {
     cudaFree(p->beta_ref); cudaFree(p->dbeta); cudaFree(p->ua); cudaFree(p->ub); cudaFree(p->cnt);
     cudaFree(p->sa); cudaFree(p->sb); cudaFree(p->blk); cudaFree(p->bk); cudaFree(p->cache);
+    cudaFree(p->ev.a); cudaFree(p->ev.b); cudaFree(p->ev.of_rec); cudaFree(p->ev.val); cudaFree(p->ev.hist);
+    cudaFree(p->ev.cursor); cudaFree(p->ev.partial);
     p->beta_ref = p->dbeta = nullptr; p->ua = p->sa = nullptr; p->ub = p->sb = nullptr; p->cnt = nullptr;
     p->blk = nullptr; p->bk = nullptr; p->cache = nullptr; p->cache_cap = 0; p->cap = 0; p->bytes = 0;
+    p->ev = Events{};
+}
+
+// Morton bits per axis for 2x2x2-voxel event bins
+int event_bin_bits(const DevScene& S) {
+    const int m = std::max(std::max((S.nx + 1) / 2, (S.ny + 1) / 2), (S.nz + 1) / 2);
+    int b = 1;
+    while ((1 << b) < m) ++b;
+    return b;
 }
 
 template <class T>
@@ -188,6 +201,8 @@ const char* pt_version(void) { return "pathrecycle 0.1 (sm_103a)"; }
 int pt::describe_scene(const pt_scene_desc* d, DevScene& S, DevCam* hc, double* tans) {
     if (!d) return fail(PT_E_INVALID, "scene description: null");
     if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(PT_E_INVALID, "grid dims must be >= 1");
+    if (d->nx > kAxisMax || d->ny > kAxisMax || d->nz > kAxisMax)
+        return fail(PT_E_INVALID, "grid dims must be <= %d per axis", kAxisMax);
     const int64_t V = (int64_t)d->nx * d->ny * d->nz;
     if (V >= (int64_t)1 << 28) return fail(PT_E_INVALID, "grid has %lld voxels; limit 2^28", (long long)V);
     if (!(d->voxel > 0.0f) || !std::isfinite(d->voxel)) return fail(PT_E_INVALID, "voxel size must be > 0");
@@ -381,6 +396,20 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
             if (created) delete p;
             return rc;
         }
+        Events& E = p->ev;
+        E.bin_bits = event_bin_bits(sc->ds);
+        E.n_bins = 1u << (3 * E.bin_bits);
+        E.cap = n * (uint64_t)sc->ds.max_orders;
+        if ((rc = dev_alloc(&E.a, E.cap, &by, "events A")) || (rc = dev_alloc(&E.b, E.cap, &by, "events B")) ||
+            (rc = dev_alloc(&E.val, E.cap, &by, "event values")) ||
+            (rc = dev_alloc(&E.of_rec, n * slots, &by, "record-to-event map")) ||
+            (rc = dev_alloc(&E.hist, E.n_bins, &by, "event bins")) ||
+            (rc = dev_alloc(&E.cursor, E.n_bins, &by, "event bin cursors")) ||
+            (rc = dev_alloc(&E.partial, 3 * 4096, &by, "scan partials"))) {
+            free_paths_buffers(p);
+            if (created) delete p;
+            return rc;
+        }
         p->cap = n;
         p->slots = slots;
         p->bytes = by;
@@ -396,6 +425,8 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
     if (int rc = launch_status("paths_store")) return rc;
     launch_sort(sbuf, n, slots, p->blk, p->bk, sc->ds.n_cams, p->sa, p->sb, st);
     if (int rc = launch_status("paths_store sort")) return rc;
+    launch_events(sc->ds, sorted_view(p), p->ev, st);
+    if (int rc = launch_status("paths_store events")) return rc;
     *pp = p;
     return PT_OK;
 }
@@ -407,7 +438,7 @@ int paths_reweight(pt_paths* p, const float* beta_t, double* images, uint32_t fl
     const pt_scene* sc = p->scene;
     float* cache = nullptr;
     if (flags & PT_CACHE) {
-        const uint64_t need = p->n * (uint64_t)sc->ds.max_orders * (uint64_t)sc->ds.n_cams;
+        const uint64_t need = p->ev.cap * (uint64_t)sc->ds.n_cams;
         if (p->cache_cap < need) {
             PT_CUDA(cudaStreamSynchronize(st));
             cudaFree(p->cache);
@@ -421,7 +452,7 @@ int paths_reweight(pt_paths* p, const float* beta_t, double* images, uint32_t fl
     }
     if (!(flags & PT_ACCUMULATE)) PT_CUDA(cudaMemsetAsync(images, 0, sizeof(double) * sc->n_pixels, st));
     launch_delta(beta_t, p->beta_ref, p->dbeta, p->V, st);
-    launch_reweight(sc->ds, sorted_view(p), beta_t, p->beta_ref, p->dbeta, images, cache, st);
+    launch_reweight(sc->ds, sorted_view(p), p->ev, beta_t, p->beta_ref, p->dbeta, images, cache, st);
     p->cache_valid = cache != nullptr;
     return launch_status("paths_reweight");
 }
@@ -435,7 +466,7 @@ int render_grad(pt_paths* p, const float* beta_t, const double* dldi, double* gr
     const pt_scene* sc = p->scene;
     if (!(flags & PT_ACCUMULATE)) PT_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * p->V, st));
     if (!(flags & PT_CACHE)) launch_delta(beta_t, p->beta_ref, p->dbeta, p->V, st);
-    launch_grad(sc->ds, sorted_view(p), beta_t, p->beta_ref, p->dbeta, dldi, grad,
+    launch_grad(sc->ds, sorted_view(p), p->ev, beta_t, p->beta_ref, p->dbeta, dldi, grad,
                 (flags & PT_CACHE) ? p->cache : nullptr, st);
     return launch_status("render_grad");
 }

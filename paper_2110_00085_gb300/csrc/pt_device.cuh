@@ -20,7 +20,6 @@ constexpr int kMaxOrders = PT_MAX_ORDERS;
 constexpr int kBuckets = PT_MAX_ORDERS + 1;
 
 // vertex record kinds (bits 28..29 of the voxel word) and path ends (30..31)
-constexpr uint32_t kVoxMask = 0x0fffffffu;
 constexpr uint32_t kKindEntry = 0u << 28;
 constexpr uint32_t kKindScatter = 1u << 28;
 enum : uint32_t { kEndNone = 0, kEndEscape = 1, kEndTrunc = 2, kEndRR = 3, kEndMiss = 4 };
@@ -100,20 +99,14 @@ __device__ __forceinline__ uint64_t fnv_word(uint64_t h, uint32_t w) {
 constexpr uint64_t kFnvBasis = 0xcbf29ce484222325ull;
 
 // ------------------------------------------------- FP32 -> FP64 widening --
-// Exact widening with integer operations only (no FP64 pipe, which is
-// narrow on GB300).  Subnormal floats flush to zero; inf/nan keep class.
+// Exact widening of finite floats with integer operations only (no FP64
+// pipe, which is narrow on GB300): the magnitude bits shift into place and
+// the exponent bias moves from 127 to 1023.  Subnormal floats flush to zero;
+// the accumulated values are finite by construction.
 __device__ __forceinline__ double widen(float f) {
     const uint32_t b = __float_as_uint(f);
-    const uint32_t e = (b >> 23) & 0xffu;
-    const uint64_t sign = (uint64_t)(b & 0x80000000u) << 32;
-    uint64_t out;
-    if (e == 0u) {
-        out = sign;
-    } else if (e == 0xffu) {
-        out = sign | (0x7ffull << 52) | ((uint64_t)(b & 0x7fffffu) << 29);
-    } else {
-        out = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7fffffu) << 29);
-    }
+    const uint64_t mag = (((uint64_t)(b & 0x7fffffffu)) << 29) + (896ull << 52);
+    const uint64_t out = ((uint64_t)(b & 0x80000000u) << 32) | ((b & 0x7f800000u) ? mag : 0ull);
     return __longlong_as_double((long long)out);
 }
 
@@ -212,8 +205,8 @@ __device__ __forceinline__ Proj project(const DevCam& k, float3 x) {
     if (!(fc >= 0.0f && fc < (float)k.W && fr >= 0.0f && fr < (float)k.H)) return p;
     p.pix = (int)fr * k.W + (int)fc;
     p.r2 = qx * qx + qy * qy + qz * qz;
-    const float r = sqrtf(p.r2);   // correctly rounded: the phase function is steep
-    p.dir = make_float3(-qx / r, -qy / r, -qz / r);
+    const float inv_r = 1.0f / sqrtf(p.r2);   // correctly rounded: the phase function is steep
+    p.dir = make_float3(-qx * inv_r, -qy * inv_r, -qz * inv_r);
     return p;
 }
 
@@ -226,64 +219,72 @@ __device__ __forceinline__ float local_contrib(float w, float fs, float beta_dra
     return ((w * (fs / beta_draw)) * T) / (r2 * omega) * inv_norm;
 }
 
+// ---------------------------------------------------------- voxel ids --
+// Vertices carry packed voxel coordinates, ix | iy << 9 | iz << 18 (grids of
+// at most 512 voxels per axis); gathers use the linear x-fastest index.
+constexpr uint32_t kVoxMask = 0x07ffffffu;
+constexpr int kAxisMax = 512;
+
+__device__ __forceinline__ uint32_t pack_vox(int ix, int iy, int iz) {
+    return (uint32_t)ix | ((uint32_t)iy << 9) | ((uint32_t)iz << 18);
+}
+__device__ __forceinline__ int lin_vox(const DevScene& S, uint32_t pv) {
+    return (int)(pv & 511u) + S.nx * ((int)((pv >> 9) & 511u) + S.ny * (int)((pv >> 18) & 511u));
+}
+__device__ __forceinline__ bool vox_ok(const DevScene& S, uint32_t pv) {
+    return (int)(pv & 511u) < S.nx && (int)((pv >> 9) & 511u) < S.ny && (int)((pv >> 18) & 511u) < S.nz;
+}
+
 // ------------------------------------------------------------------ DDA --
 // Traversal of the voxels cut by p + t d, t in [0, tmax] (clipped to the
-// box), starting in voxel (ix, iy, iz) that contains p.  Face crossings are
-// recomputed from the face index each step (no accumulated error); ties
-// step x before y before z; zero-length crossings are visited with length 0.
+// box), starting in the voxel (ix, iy, iz) that contains p.  Per axis the
+// k-th face crossed after the start lies at t = t0 + k D (t0 the first face,
+// D = voxel / |d| the spacing), one rounding from its exact value; the
+// three candidates are recomputed every step without branches.  Ties step x
+// before y before z; zero-length crossings are visited with length 0.  The
+// box exit bounds the walk (the exit face has the same formula), and an
+// index check with a step budget records an error instead of running off.
 struct Dda {
-    float px, py, pz;
-    float ivx, ivy, ivz;   // 1/d per axis
-    float kx, ky, kz;      // index of the next face per axis
-    float tnx, tny, tnz;   // t of that face
-    float gx, gy, gz;      // step (+1 / -1)
-    int dx, dy, dz;        // linear-index step
+    float tnx, tny, tnz;   // t of the next face per axis
+    float kx, ky, kz;      // faces crossed so far per axis
+    float Dx, Dy, Dz;      // face spacing per axis
+    float Ax, Ay, Az;      // t of the first face per axis
+    int sx, sy, sz;        // linear-index step per axis
     int idx;
     float t, tend;
-    int iter, max_iter;
+    int budget;
+
+    __device__ __forceinline__ void axis(float pc, float dc, int ic, int n, float o, float vox, int stride, float& tn,
+                                         float& k, float& D, float& A, int& si) {
+        const float INF = __int_as_float(0x7f800000);
+        k = 0.0f;
+        if (dc != 0.0f) {
+            const float inv = 1.0f / dc;
+            D = vox * fabsf(inv);
+            const bool up = dc > 0.0f;
+            A = (fmaf((float)(up ? ic + 1 : ic), vox, o) - pc) * inv;
+            si = up ? stride : -stride;
+            tn = A;
+            tend = fminf(tend, fmaf((float)(up ? n - 1 - ic : ic), D, A));   // exit face
+        } else {
+            D = 0.0f;
+            A = INF;
+            si = 0;
+            tn = INF;
+        }
+    }
 
     __device__ __forceinline__ void init(const DevScene& S, float3 p, float3 d, int ix, int iy, int iz, float tmax) {
-        px = p.x; py = p.y; pz = p.z;
         idx = ix + S.nx * (iy + S.ny * iz);
         t = 0.0f;
         tend = tmax;
-        iter = 0;
-        max_iter = S.nx + S.ny + S.nz + 4;
-        const float INF = __int_as_float(0x7f800000);
-        // x
-        if (d.x != 0.0f) {
-            ivx = 1.0f / d.x;
-            gx = d.x > 0.0f ? 1.0f : -1.0f;
-            kx = (float)(d.x > 0.0f ? ix + 1 : ix);
-            dx = d.x > 0.0f ? 1 : -1;
-            tnx = (fmaf(kx, S.vox, S.ox) - px) * ivx;
-            const float te = (fmaf(d.x > 0.0f ? (float)S.nx : 0.0f, S.vox, S.ox) - px) * ivx;
-            tend = fminf(tend, te);
-        } else {
-            ivx = 0.0f; gx = 0.0f; kx = 0.0f; dx = 0; tnx = INF;
-        }
-        if (d.y != 0.0f) {
-            ivy = 1.0f / d.y;
-            gy = d.y > 0.0f ? 1.0f : -1.0f;
-            ky = (float)(d.y > 0.0f ? iy + 1 : iy);
-            dy = d.y > 0.0f ? S.nx : -S.nx;
-            tny = (fmaf(ky, S.vox, S.oy) - py) * ivy;
-            const float te = (fmaf(d.y > 0.0f ? (float)S.ny : 0.0f, S.vox, S.oy) - py) * ivy;
-            tend = fminf(tend, te);
-        } else {
-            ivy = 0.0f; gy = 0.0f; ky = 0.0f; dy = 0; tny = INF;
-        }
-        if (d.z != 0.0f) {
-            ivz = 1.0f / d.z;
-            gz = d.z > 0.0f ? 1.0f : -1.0f;
-            kz = (float)(d.z > 0.0f ? iz + 1 : iz);
-            dz = d.z > 0.0f ? S.nx * S.ny : -S.nx * S.ny;
-            tnz = (fmaf(kz, S.vox, S.oz) - pz) * ivz;
-            const float te = (fmaf(d.z > 0.0f ? (float)S.nz : 0.0f, S.vox, S.oz) - pz) * ivz;
-            tend = fminf(tend, te);
-        } else {
-            ivz = 0.0f; gz = 0.0f; kz = 0.0f; dz = 0; tnz = INF;
-        }
+        budget = S.nx + S.ny + S.nz + 4;
+        axis(p.x, d.x, ix, S.nx, S.ox, S.vox, 1, tnx, kx, Dx, Ax, sx);
+        axis(p.y, d.y, iy, S.ny, S.oy, S.vox, S.nx, tny, ky, Dy, Ay, sy);
+        axis(p.z, d.z, iz, S.nz, S.oz, S.vox, S.nx * S.ny, tnz, kz, Dz, Az, sz);
+    }
+    __device__ __forceinline__ void init(const DevScene& S, float3 p, float3 d, uint32_t pv, float tmax) {
+        init(S, p, d, (int)(pv & 511u), (int)((pv >> 9) & 511u), (int)((pv >> 18) & 511u), tmax);
     }
 
     // t of the next face crossing
@@ -295,46 +296,38 @@ struct Dda {
     // move into the next voxel; false when the ray ended or an invariant broke
     __device__ __forceinline__ bool step(const DevScene& S, float tn) {
         if (tn >= tend) return false;
-        if (tnx <= tny && tnx <= tnz) {
-            kx += gx;
-            idx += dx;
-            tnx = (fmaf(kx, S.vox, S.ox) - px) * ivx;
-        } else if (tny <= tnz) {
-            ky += gy;
-            idx += dy;
-            tny = (fmaf(ky, S.vox, S.oy) - py) * ivy;
-        } else {
-            kz += gz;
-            idx += dz;
-            tnz = (fmaf(kz, S.vox, S.oz) - pz) * ivz;
-        }
+        const bool mx = tnx == tn;
+        const bool my = !mx && tny == tn;
+        const bool mz = !mx && !my;
+        kx = mx ? kx + 1.0f : kx;
+        ky = my ? ky + 1.0f : ky;
+        kz = mz ? kz + 1.0f : kz;
+        idx += mx ? sx : (my ? sy : sz);
+        tnx = fmaf(kx, Dx, Ax);
+        tny = fmaf(ky, Dy, Ay);
+        tnz = fmaf(kz, Dz, Az);
         t = fmaxf(t, tn);
-        if ((unsigned)idx >= (unsigned)S.V) {
-            atomicOr(S.err, kErrIndex);
-            return false;
-        }
-        if (++iter > max_iter) {
-            atomicOr(S.err, kErrIter);
+        if ((unsigned)idx >= (unsigned)S.V || --budget < 0) {
+            atomicOr(S.err, (unsigned)idx >= (unsigned)S.V ? kErrIndex : kErrIter);
             return false;
         }
         return true;
     }
-};
 
-__device__ __forceinline__ void voxel_coords(const DevScene& S, int v, int& ix, int& iy, int& iz) {
-    ix = v % S.nx;
-    const int r = v / S.nx;
-    iy = r % S.ny;
-    iz = r / S.ny;
-}
+    // packed coordinates of the current voxel, given the start voxel and d
+    __device__ __forceinline__ uint32_t coords(uint32_t pv0, float3 d) const {
+        const int cx = (int)(pv0 & 511u) + (d.x > 0.0f ? (int)kx : -(int)kx);
+        const int cy = (int)((pv0 >> 9) & 511u) + (d.y > 0.0f ? (int)ky : -(int)ky);
+        const int cz = (int)((pv0 >> 18) & 511u) + (d.z > 0.0f ? (int)kz : -(int)kz);
+        return pack_vox(cx, cy, cz);
+    }
+};
 
 // optical depth of the grid `beta` (+ air) from p along d to the box exit
 __device__ __forceinline__ float optical_depth_to_exit(const DevScene& S, const float* __restrict__ beta, float3 p,
-                                                       float3 d, int v, int* crossings) {
-    int ix, iy, iz;
-    voxel_coords(S, v, ix, iy, iz);
+                                                       float3 d, uint32_t pv, int* crossings) {
     Dda r;
-    r.init(S, p, d, ix, iy, iz, __int_as_float(0x7f800000));
+    r.init(S, p, d, pv, __int_as_float(0x7f800000));
     float tau = 0.0f;
     int n = 0;
     for (;;) {
@@ -348,12 +341,10 @@ __device__ __forceinline__ float optical_depth_to_exit(const DevScene& S, const 
 }
 
 // scatter -s * l_v into grad over the voxels of the ray p + t d, t <= tmax
-__device__ __forceinline__ void scatter_ray(const DevScene& S, double* __restrict__ grad, float3 p, float3 d, int v,
-                                            float tmax, float s) {
-    int ix, iy, iz;
-    voxel_coords(S, v, ix, iy, iz);
+__device__ __forceinline__ void scatter_ray(const DevScene& S, double* __restrict__ grad, float3 p, float3 d,
+                                            uint32_t pv, float tmax, float s) {
     Dda r;
-    r.init(S, p, d, ix, iy, iz, tmax);
+    r.init(S, p, d, pv, tmax);
     for (;;) {
         const float tn = r.next();
         const float l = r.seg(tn);
@@ -364,11 +355,9 @@ __device__ __forceinline__ void scatter_ray(const DevScene& S, double* __restric
 
 // sum of dbeta * l over the segment p + t d, t <= tmax (stored flight)
 __device__ __forceinline__ float delta_depth(const DevScene& S, const float* __restrict__ dbeta, float3 p, float3 d,
-                                             int v, float tmax) {
-    int ix, iy, iz;
-    voxel_coords(S, v, ix, iy, iz);
+                                             uint32_t pv, float tmax) {
     Dda r;
-    r.init(S, p, d, ix, iy, iz, tmax);
+    r.init(S, p, d, pv, tmax);
     float acc = 0.0f;
     for (;;) {
         const float tn = r.next();
@@ -380,11 +369,11 @@ __device__ __forceinline__ float delta_depth(const DevScene& S, const float* __r
 
 // -------------------------------------------------------- path records --
 // Vertex record, two 16-byte streams:
-//   A = {x, y, z (float bits), voxel | kind << 28 | end << 30}
+//   A = {x, y, z (float bits), packed voxel | kind << 28 | end << 30}
 //   B = {incoming direction x, y, z, length of the flight into the vertex}
 // Vertex 0 is the box entry (incoming = sun direction, length 0).
-__device__ __forceinline__ uint4 rec_a(float3 x, int v, uint32_t kind) {
-    return make_uint4(__float_as_uint(x.x), __float_as_uint(x.y), __float_as_uint(x.z), ((uint32_t)v & kVoxMask) | kind);
+__device__ __forceinline__ uint4 rec_a(float3 x, uint32_t pv, uint32_t kind) {
+    return make_uint4(__float_as_uint(x.x), __float_as_uint(x.y), __float_as_uint(x.z), (pv & kVoxMask) | kind);
 }
 
 }  // namespace pt

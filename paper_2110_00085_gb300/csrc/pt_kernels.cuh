@@ -23,7 +23,23 @@ struct Buckets {
     uint64_t count[kBuckets];
     uint64_t path_off[kBuckets + 1];
     uint64_t rec_off[kBuckets + 1];
-    uint64_t cache_off[kBuckets + 1];   // floats, (event, camera)-major
+    uint64_t n_events;                  // collision vertices of the stored paths
+};
+
+// Collision vertices ("events") of the stored paths, binned by the Morton
+// code of their 2x2x2-voxel block: neighbouring events share a warp, so
+// their shadow rays to a camera start together and run side by side.
+struct Events {
+    uint4* a;          // {x, y, z bits, packed voxel}
+    float4* b;         // {incoming direction, W: path weight before the vertex}
+    uint32_t* of_rec;  // event slot of each sorted record (slots >= 1)
+    float* val;        // per-event scalar (gradient: sum over cameras of a)
+    uint32_t* hist;    // per bin
+    uint32_t* cursor;  // per bin: exclusive offsets, then fill positions
+    uint32_t* partial; // block sums of the scan
+    uint32_t n_bins;
+    int bin_bits;      // Morton bits per axis
+    uint64_t cap;      // event capacity
 };
 
 struct SortedPaths {
@@ -34,6 +50,45 @@ struct SortedPaths {
     float inv_norm;
 };
 
+// ------------------------------------------ stored-path access helpers --
+struct PathRef {
+    int B;
+    uint64_t base;    // record (slot 0)
+    uint64_t stride;  // records between slots
+};
+
+__device__ __forceinline__ bool locate(const uint64_t* po, const uint64_t* ro, const uint64_t* cnt, int max_orders,
+                                       uint64_t j, PathRef& r) {
+    for (int b = 1; b <= max_orders; ++b) {
+        if (j >= po[b] && j < po[b + 1]) {
+            const uint64_t pos = j - po[b];
+            r.B = b;
+            r.stride = cnt[b];
+            r.base = ro[b] + pos;
+            return true;
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ float3 xyz(uint4 a) {
+    return make_float3(__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z));
+}
+
+struct SharedBk {
+    uint64_t po[kBuckets + 1], ro[kBuckets + 1], cnt[kBuckets];
+};
+
+__device__ __forceinline__ void load_shared(const DevScene& S, const SortedPaths& P, DevCam* cams, SharedBk& sb) {
+    for (int c = threadIdx.x; c < S.n_cams; c += blockDim.x) cams[c] = S.cams[c];
+    for (int k = threadIdx.x; k <= kBuckets; k += blockDim.x) {
+        sb.po[k] = P.buckets->path_off[k];
+        sb.ro[k] = P.buckets->rec_off[k];
+        if (k < kBuckets) sb.cnt[k] = P.buckets->count[k];
+    }
+    __syncthreads();
+}
+
 void launch_sample(const DevScene& S, const float* beta, uint64_t first, uint64_t n, float inv_norm, uint64_t seed,
                    uint32_t epoch, double* images, double* tallies, uint64_t* fps, const StoreBuf* store,
                    cudaStream_t st);
@@ -41,13 +96,20 @@ void launch_sample(const DevScene& S, const float* beta, uint64_t first, uint64_
 void launch_sort(const StoreBuf& in, uint64_t n, int n_buckets, uint32_t* blk_hist, Buckets* buckets, int n_cams,
                  uint4* out_a, float4* out_b, cudaStream_t st);
 
-void launch_reweight(const DevScene& S, const SortedPaths& P, const float* beta_t, const float* beta_ref,
-                     const float* dbeta, double* images, float* cache, cudaStream_t st);
+void launch_events(const DevScene& S, const SortedPaths& P, const Events& E, cudaStream_t st);
 
-void launch_grad(const DevScene& S, const SortedPaths& P, const float* beta_t, const float* beta_ref,
-                 const float* dbeta, const double* dldi, double* grad, const float* cache, cudaStream_t st);
+void launch_reweight(const DevScene& S, const SortedPaths& P, const Events& E, const float* beta_t,
+                     const float* beta_ref, const float* dbeta, double* images, float* cache, cudaStream_t st);
+
+void launch_grad(const DevScene& S, const SortedPaths& P, const Events& E, const float* beta_t,
+                 const float* beta_ref, const float* dbeta, const double* dldi, double* grad, const float* cache,
+                 cudaStream_t st);
 
 void launch_delta(const float* a, const float* b, float* out, int64_t n, cudaStream_t st);
+
+// gradient without a contribution cache: per path, re-traces the shadow rays
+void launch_grad_reference(const DevScene& S, const SortedPaths& P, const float* beta_t, const float* beta_ref,
+                           const float* dbeta, const double* dldi, double* grad, cudaStream_t st);
 
 // host side (pt_api.cu): record an error message for pt_last_error() and
 // return `code`; validate a scene description and derive its constants

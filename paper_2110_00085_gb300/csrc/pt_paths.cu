@@ -77,25 +77,21 @@ __global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ blk_h
     if (threadIdx.x == 1023) bk->count[blockIdx.x] = part[1023];
 }
 
-__global__ void k_bucket_offsets(Buckets* bk, int n_buckets, int n_cams) {
+__global__ void k_bucket_offsets(Buckets* bk, int n_buckets) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    uint64_t p = 0, r = 0, c = 0;
-    bk->path_off[0] = 0;
-    bk->rec_off[0] = 0;
-    bk->cache_off[0] = 0;
+    uint64_t p = 0, r = 0, ev = 0;
     for (int b = 0; b < kBuckets; ++b) {
         const uint64_t n = (b >= 1 && b < n_buckets) ? bk->count[b] : 0;   // B = 0 paths are not stored
         if (b >= n_buckets) bk->count[b] = 0;
-        bk->path_off[b + 1] = p + n;
-        bk->rec_off[b + 1] = r + n * (uint64_t)(b + 1);
-        bk->cache_off[b + 1] = c + n * (uint64_t)b * (uint64_t)n_cams;
         bk->path_off[b] = p;
         bk->rec_off[b] = r;
-        bk->cache_off[b] = c;
         p += n;
         r += n * (uint64_t)(b + 1);
-        c += n * (uint64_t)b * (uint64_t)n_cams;
+        ev += n * (uint64_t)b;
     }
+    bk->path_off[kBuckets] = p;
+    bk->rec_off[kBuckets] = r;
+    bk->n_events = ev;
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(StoreBuf in, uint64_t n, const uint32_t* __restrict__ blk_off,
@@ -129,90 +125,55 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(StoreBuf in, uint
     }
 }
 
-// ---------------------------------------------------- recycled passes --
-struct PathRef {
-    int B;
-    uint64_t base;    // record (slot 0)
-    uint64_t stride;  // records between slots
-    uint64_t cbase;   // cache (event 1, camera 0)
-    uint64_t cstride;
-};
-
-__device__ __forceinline__ bool locate(const uint64_t* po, const uint64_t* ro, const uint64_t* co,
-                                       const uint64_t* cnt, int max_orders, uint64_t j, PathRef& r) {
-    for (int b = 1; b <= max_orders; ++b) {
-        if (j >= po[b] && j < po[b + 1]) {
-            const uint64_t pos = j - po[b];
-            r.B = b;
-            r.stride = cnt[b];
-            r.base = ro[b] + pos;
-            r.cbase = co[b] + pos;
-            r.cstride = cnt[b];
-            return true;
-        }
-    }
-    return false;
-}
-
-__device__ __forceinline__ float3 xyz(uint4 a) {
-    return make_float3(__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z));
-}
-
-struct SharedBk {
-    uint64_t po[kBuckets + 1], ro[kBuckets + 1], co[kBuckets + 1], cnt[kBuckets];
-};
-
-__device__ __forceinline__ void load_shared(const DevScene& S, const SortedPaths& P, DevCam* cams, SharedBk& sb) {
-    for (int c = threadIdx.x; c < S.n_cams; c += blockDim.x) cams[c] = S.cams[c];
-    for (int k = threadIdx.x; k <= kBuckets; k += blockDim.x) {
-        sb.po[k] = P.buckets->path_off[k];
-        sb.ro[k] = P.buckets->rec_off[k];
-        sb.co[k] = P.buckets->cache_off[k];
-        if (k < kBuckets) sb.cnt[k] = P.buckets->count[k];
-    }
-    __syncthreads();
-}
-
-template <bool CACHE>
-__global__ void __launch_bounds__(128) k_reweight(DevScene S, SortedPaths P, const float* __restrict__ beta_t,
-                                                  const float* __restrict__ beta_ref, const float* __restrict__ dbeta,
-                                                  double* __restrict__ images, float* __restrict__ cache) {
+// gradient without a contribution cache (reference form): per path,
+// phase 1 re-traces every shadow ray for its transmittance, scatters it at
+// once and adds the local-estimate vertex term; phase 2 walks the stored
+// flights backwards with the suffix sums S_k.
+__global__ void __launch_bounds__(128) k_grad(DevScene S, SortedPaths P, const float* __restrict__ beta_t,
+                                              const float* __restrict__ beta_ref, const float* __restrict__ dbeta,
+                                              const double* __restrict__ dldi, double* __restrict__ grad) {
     __shared__ DevCam cams[kMaxCams];
     __shared__ SharedBk sb;
     load_shared(S, P, cams, sb);
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     PathRef pr;
-    if (!locate(sb.po, sb.ro, sb.co, sb.cnt, S.max_orders, j, pr)) return;
+    if (!locate(sb.po, sb.ro, sb.cnt, S.max_orders, j, pr)) return;
+    float Aev[kMaxOrders + 1];
     uint4 a0 = P.rec_a[pr.base];
     float3 xp = xyz(a0);
-    int vp = (int)(a0.w & kVoxMask);
+    uint32_t pvp = a0.w & kVoxMask;
     float w = S.w0;
     float4 bin = P.rec_b[pr.base + pr.stride];
+    // ---- phase 1: events (shadow rays and local-estimate vertex terms) ----
     for (int e = 1; e <= pr.B; ++e) {
         const uint4 ra = P.rec_a[pr.base + (uint64_t)e * pr.stride];
         const float3 om = make_float3(bin.x, bin.y, bin.z);
         const float3 x = xyz(ra);
-        const int v = (int)(ra.w & kVoxMask);
-        if ((unsigned)v >= (unsigned)S.V || (unsigned)vp >= (unsigned)S.V) {
+        const uint32_t pv = ra.w & kVoxMask;
+        if (!vox_ok(S, pv) || !vox_ok(S, pvp)) {
             atomicOr(S.err, kErrRecord);
             return;
         }
-        // flight e: transmittance ratio under beta_t vs beta_ref
-        const float W = w * expf(-delta_depth(S, dbeta, xp, om, vp, bin.w));
+        const int v = lin_vox(S, pv);
         const float bct = __ldg(beta_t + v), bcr = __ldg(beta_ref + v);
         const float btr = bcr + S.beta_air;
+        const float W = w * expf(-delta_depth(S, dbeta, xp, om, pvp, bin.w));
+        float A = 0.0f;
         for (int c = 0; c < S.n_cams; ++c) {
             const Proj q = project(cams[c], x);
-            float ev = 0.0f;
-            if (q.pix >= 0) {
-                const float T = expf(-optical_depth_to_exit(S, beta_t, x, q.dir, v, nullptr));
-                const float mu = dot3(om, q.dir);
-                const int gp = cams[c].off + q.pix;
-                ev = local_contrib(W, fs_medium(S, bct, mu), btr, T, q.r2, __ldg(S.omega + gp), P.inv_norm);
-                red_add(images + gp, ev);
-            }
-            if (CACHE) cache[pr.cbase + ((uint64_t)(e - 1) * S.n_cams + c) * pr.cstride] = ev;
+            if (q.pix < 0) continue;
+            const int gp = cams[c].off + q.pix;
+            const float mu = dot3(om, q.dir);
+            const float T = expf(-optical_depth_to_exit(S, beta_t, x, q.dir, pv, nullptr));
+            const float ev = local_contrib(W, fs_medium(S, bct, mu), btr, T, q.r2, __ldg(S.omega + gp), P.inv_norm);
+            if (ev == 0.0f) continue;
+            const float a = (float)__ldg(dldi + gp) * ev;
+            if (a == 0.0f) continue;
+            A += a;
+            scatter_ray(S, grad, x, q.dir, pv, __int_as_float(0x7f800000), a);
+            red_add(grad + v, a * score_vertex(S, bct, mu));
         }
+        Aev[e] = A;
         if (e < pr.B) {
             const float4 bnext = P.rec_b[pr.base + (uint64_t)(e + 1) * pr.stride];
             const float mu = om.x * bnext.x + om.y * bnext.y + om.z * bnext.z;
@@ -227,77 +188,7 @@ __global__ void __launch_bounds__(128) k_reweight(DevScene S, SortedPaths P, con
             bin = bnext;
         }
         xp = x;
-        vp = v;
-    }
-}
-
-template <bool CACHE>
-__global__ void __launch_bounds__(128) k_grad(DevScene S, SortedPaths P, const float* __restrict__ beta_t,
-                                              const float* __restrict__ beta_ref, const float* __restrict__ dbeta,
-                                              const double* __restrict__ dldi, double* __restrict__ grad,
-                                              const float* __restrict__ cache) {
-    __shared__ DevCam cams[kMaxCams];
-    __shared__ SharedBk sb;
-    load_shared(S, P, cams, sb);
-    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    PathRef pr;
-    if (!locate(sb.po, sb.ro, sb.co, sb.cnt, S.max_orders, j, pr)) return;
-    float Aev[kMaxOrders + 1];
-    uint4 a0 = P.rec_a[pr.base];
-    float3 xp = xyz(a0);
-    int vp = (int)(a0.w & kVoxMask);
-    float w = S.w0;
-    float4 bin = P.rec_b[pr.base + pr.stride];
-    // ---- phase 1: events (shadow rays and local-estimate vertex terms) ----
-    for (int e = 1; e <= pr.B; ++e) {
-        const uint4 ra = P.rec_a[pr.base + (uint64_t)e * pr.stride];
-        const float3 om = make_float3(bin.x, bin.y, bin.z);
-        const float3 x = xyz(ra);
-        const int v = (int)(ra.w & kVoxMask);
-        if ((unsigned)v >= (unsigned)S.V || (unsigned)vp >= (unsigned)S.V) {
-            atomicOr(S.err, kErrRecord);
-            return;
-        }
-        const float bct = __ldg(beta_t + v), bcr = __ldg(beta_ref + v);
-        const float btr = bcr + S.beta_air;
-        float W = 0.0f;
-        if (!CACHE) W = w * expf(-delta_depth(S, dbeta, xp, om, vp, bin.w));
-        float A = 0.0f;
-        for (int c = 0; c < S.n_cams; ++c) {
-            const Proj q = project(cams[c], x);
-            if (q.pix < 0) continue;
-            const int gp = cams[c].off + q.pix;
-            const float mu = dot3(om, q.dir);
-            float ev;
-            if (CACHE) {
-                ev = cache[pr.cbase + ((uint64_t)(e - 1) * S.n_cams + c) * pr.cstride];
-            } else {
-                const float T = expf(-optical_depth_to_exit(S, beta_t, x, q.dir, v, nullptr));
-                ev = local_contrib(W, fs_medium(S, bct, mu), btr, T, q.r2, __ldg(S.omega + gp), P.inv_norm);
-            }
-            if (ev == 0.0f) continue;
-            const float a = (float)__ldg(dldi + gp) * ev;
-            if (a == 0.0f) continue;
-            A += a;
-            scatter_ray(S, grad, x, q.dir, v, __int_as_float(0x7f800000), a);
-            red_add(grad + v, a * score_vertex(S, bct, mu));
-        }
-        Aev[e] = A;
-        if (!CACHE && e < pr.B) {
-            const float4 bnext = P.rec_b[pr.base + (uint64_t)(e + 1) * pr.stride];
-            const float mu = om.x * bnext.x + om.y * bnext.y + om.z * bnext.z;
-            const float fsr = fs_medium(S, bcr, mu);
-            if (fsr == 0.0f) {
-                w = 0.0f;
-            } else {
-                const float albr = (S.alb_c * bcr + S.alb_a * S.beta_air) / btr;
-                w = W * (albr * (fs_medium(S, bct, mu) / fsr));
-                if (e >= S.rr_start) w *= S.inv_q;
-            }
-        }
-        if (e < pr.B) bin = P.rec_b[pr.base + (uint64_t)(e + 1) * pr.stride];
-        xp = x;
-        vp = v;
+        pvp = pv;
     }
     // ---- phase 2: flights and scattering vertices, suffix sums ----
     float Ssum = 0.0f;
@@ -308,13 +199,13 @@ __global__ void __launch_bounds__(128) k_grad(DevScene S, SortedPaths P, const f
             // vertex e: angle between the flight into it and the flight out
             const float4 bn = P.rec_b[pr.base + (uint64_t)(e + 1) * pr.stride];
             const float mu = be.x * bn.x + be.y * bn.y + be.z * bn.z;
-            const int v = (int)(ra.w & kVoxMask);
+            const int v = lin_vox(S, ra.w & kVoxMask);
             red_add(grad + v, Ssum * score_vertex(S, __ldg(beta_t + v), mu));
         }
         Ssum += Aev[e];
         if (Ssum != 0.0f) {
             const uint4 rp = P.rec_a[pr.base + (uint64_t)(e - 1) * pr.stride];
-            scatter_ray(S, grad, xyz(rp), make_float3(be.x, be.y, be.z), (int)(rp.w & kVoxMask), be.w, Ssum);
+            scatter_ray(S, grad, xyz(rp), make_float3(be.x, be.y, be.z), rp.w & kVoxMask, be.w, Ssum);
         }
     }
 }
@@ -333,28 +224,15 @@ void launch_sort(const StoreBuf& in, uint64_t n, int n_buckets, uint32_t* blk_hi
     const uint32_t nblk = blocks_for(n, kSortThreads);
     k_sort_count<<<nblk, kSortThreads, 0, st>>>(in.cnt, n, blk_hist, nblk);
     k_sort_scan<<<kBuckets, 1024, 0, st>>>(blk_hist, nblk, buckets);
-    k_bucket_offsets<<<1, 32, 0, st>>>(buckets, n_buckets, n_cams);
+    k_bucket_offsets<<<1, 32, 0, st>>>(buckets, n_buckets);
     k_sort_scatter<<<nblk, kSortThreads, 0, st>>>(in, n, blk_hist, nblk, buckets, out_a, out_b);
 }
 
-void launch_reweight(const DevScene& S, const SortedPaths& P, const float* beta_t, const float* beta_ref,
-                     const float* dbeta, double* images, float* cache, cudaStream_t st) {
+void launch_grad_reference(const DevScene& S, const SortedPaths& P, const float* beta_t, const float* beta_ref,
+                           const float* dbeta, const double* dldi, double* grad, cudaStream_t st) {
     const unsigned g = blocks_for(P.n_max, 128);
     if (g == 0) return;
-    if (cache)
-        k_reweight<true><<<g, 128, 0, st>>>(S, P, beta_t, beta_ref, dbeta, images, cache);
-    else
-        k_reweight<false><<<g, 128, 0, st>>>(S, P, beta_t, beta_ref, dbeta, images, nullptr);
-}
-
-void launch_grad(const DevScene& S, const SortedPaths& P, const float* beta_t, const float* beta_ref,
-                 const float* dbeta, const double* dldi, double* grad, const float* cache, cudaStream_t st) {
-    const unsigned g = blocks_for(P.n_max, 128);
-    if (g == 0) return;
-    if (cache)
-        k_grad<true><<<g, 128, 0, st>>>(S, P, beta_t, beta_ref, dbeta, dldi, grad, cache);
-    else
-        k_grad<false><<<g, 128, 0, st>>>(S, P, beta_t, beta_ref, dbeta, dldi, grad, nullptr);
+    k_grad<<<g, 128, 0, st>>>(S, P, beta_t, beta_ref, dbeta, dldi, grad);
 }
 
 void launch_delta(const float* a, const float* b, float* out, int64_t n, cudaStream_t st) {

@@ -72,22 +72,21 @@ __device__ __forceinline__ void trace_one(const DevScene& S, const DevCam* cams,
         int vy = min(max((int)floorf((x.y - S.oy) * S.inv_vox), 0), S.ny - 1);
         int vz = min(max((int)floorf((x.z - S.oz) * S.inv_vox), 0), S.nz - 1);
         int v = vx + S.nx * (vy + S.ny * vz);
+        uint32_t pv = pack_vox(vx, vy, vz);
         float3 om = sd;
         float w = S.w0;
         float tau = -logf(u.z);
         if (TALLY) { tal[PT_T_INJECTED] += S.w0; tal[PT_T_ENTERED] += 1.0f; }
         if (STORE) {
-            st.rec_a[i] = rec_a(x, v, kKindEntry);
+            st.rec_a[i] = rec_a(x, pv, kKindEntry);
             st.rec_b[i] = make_float4(sd.x, sd.y, sd.z, 0.0f);
         }
         int B = 0;
         uint32_t end = kEndNone;
         for (int k = 1;; ++k) {
             // ---- distance sampling (regular tracking through the grid) ----
-            int ix, iy, iz;
-            voxel_coords(S, v, ix, iy, iz);
             Dda r;
-            r.init(S, x, om, ix, iy, iz, __int_as_float(0x7f800000));
+            r.init(S, x, om, pv, __int_as_float(0x7f800000));
             float tcol = -1.0f;
             int ncross = 0;
             // remaining optical depth kept as tau + comp (compensated: the
@@ -119,10 +118,11 @@ __device__ __forceinline__ void trace_one(const DevScene& S, const DevCam* cams,
                 break;
             }
             v = r.idx;
+            pv = r.coords(pv, om);
             x = make_float3(fmaf(tcol, om.x, x.x), fmaf(tcol, om.y, x.y), fmaf(tcol, om.z, x.z));
             B = k;
             if (STORE) {
-                st.rec_a[(uint64_t)k * st.stride + i] = rec_a(x, v, kKindScatter);
+                st.rec_a[(uint64_t)k * st.stride + i] = rec_a(x, pv, kKindScatter);
                 st.rec_b[(uint64_t)k * st.stride + i] = make_float4(om.x, om.y, om.z, tcol);
             }
             const float bc = __ldg(beta + v);
@@ -136,7 +136,7 @@ __device__ __forceinline__ void trace_one(const DevScene& S, const DevCam* cams,
                 if (FP) h = fnv_word(h, (uint32_t)pr.pix);
                 if (!IMG || pr.pix < 0) continue;
                 int nc = 0;
-                const float T = expf(-optical_depth_to_exit(S, beta, x, pr.dir, v, TALLY ? &nc : nullptr));
+                const float T = expf(-optical_depth_to_exit(S, beta, x, pr.dir, pv, TALLY ? &nc : nullptr));
                 const float mu = dot3(om, pr.dir);
                 const int gp = cams[c].off + pr.pix;
                 const float ev = local_contrib(w, fs_medium(S, bc, mu), bt, T, pr.r2, __ldg(S.omega + gp), inv_norm);
