@@ -156,9 +156,9 @@ void free_paths_buffers(pt_paths* p) {
     p->ev = Events{};
 }
 
-// Morton bits per axis for 2x2x2-voxel event bins
+// Morton bits per axis for per-voxel event bins
 int event_bin_bits(const DevScene& S) {
-    const int m = std::max(std::max((S.nx + 1) / 2, (S.ny + 1) / 2), (S.nz + 1) / 2);
+    const int m = std::max(std::max(S.nx, S.ny), S.nz);
     int b = 1;
     while ((1 << b) < m) ++b;
     return b;
@@ -398,6 +398,11 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
         }
         Events& E = p->ev;
         E.bin_bits = event_bin_bits(sc->ds);
+        E.bin_shift = 0;
+        while (E.bin_bits > 8) {   // keep the two-level bin scan within 2^24 bins
+            --E.bin_bits;
+            ++E.bin_shift;
+        }
         E.n_bins = 1u << (3 * E.bin_bits);
         E.cap = n * (uint64_t)sc->ds.max_orders;
         if ((rc = dev_alloc(&E.a, E.cap, &by, "events A")) || (rc = dev_alloc(&E.b, E.cap, &by, "events B")) ||

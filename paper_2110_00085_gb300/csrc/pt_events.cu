@@ -12,10 +12,11 @@
 //               optional cache) and, for the gradient, shadow-ray scatters
 //               -a l and local-estimate vertex terms, A_e = sum_d a.
 // Paths are fixed for N_r steps, so events are binned once per store by the
-// Morton code of their 2x2x2-voxel block (the paper's path sorting applied
-// to collision points): the 32 events of a warp lie close together, their
-// shadow rays to one camera start together, run nearly parallel through the
-// same voxels (shared cache lines) and end at nearly the same box exit.
+// Morton code of their voxel (the paper's path sorting applied to collision
+// points): the 32 events of a warp lie close together -- events of one voxel
+// on adjacent lanes -- so their shadow rays to one camera start together, run
+// nearly parallel through the same voxels (shared cache lines) and end at
+// nearly the same box exit.
 #include "pt_kernels.cuh"
 
 namespace pt {
@@ -32,9 +33,9 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
     v = (v | (v << 2)) & 0x09249249u;
     return v;
 }
-__device__ __forceinline__ uint32_t event_bin(uint32_t pv, int bits) {
-    const uint32_t bx = (pv & 511u) >> 1, by = ((pv >> 9) & 511u) >> 1, bz = ((pv >> 18) & 511u) >> 1;
+__device__ __forceinline__ uint32_t event_bin(uint32_t pv, int bits, int shift) {
     const uint32_t m = (1u << bits) - 1u;
+    const uint32_t bx = (pv & 511u) >> shift, by = ((pv >> 9) & 511u) >> shift, bz = ((pv >> 18) & 511u) >> shift;
     return spread3(bx & m) | (spread3(by & m) << 1) | (spread3(bz & m) << 2);
 }
 
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(128) k_ev_hist(SortedPaths P, Events E, int ma
     if (!locate(sb.po, sb.ro, sb.cnt, max_orders, j, pr)) return;
     for (int e = 1; e <= pr.B; ++e) {
         const uint32_t pv = P.rec_a[pr.base + (uint64_t)e * pr.stride].w & kVoxMask;
-        atomicAdd(E.hist + event_bin(pv, E.bin_bits), 1u);
+        atomicAdd(E.hist + event_bin(pv, E.bin_bits, E.bin_shift), 1u);
     }
 }
 
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(128) k_ev_scatter(SortedPaths P, Events E, int
         const uint64_t rec = pr.base + (uint64_t)e * pr.stride;
         const uint4 a = P.rec_a[rec];
         const float4 b = P.rec_b[rec];
-        const uint32_t pos = atomicAdd(E.cursor + event_bin(a.w & kVoxMask, E.bin_bits), 1u);
+        const uint32_t pos = atomicAdd(E.cursor + event_bin(a.w & kVoxMask, E.bin_bits, E.bin_shift), 1u);
         E.a[pos] = make_uint4(a.x, a.y, a.z, a.w & kVoxMask);
         E.b[pos] = make_float4(b.x, b.y, b.z, 0.0f);
         E.of_rec[rec] = pos;
@@ -247,39 +248,98 @@ __global__ void __launch_bounds__(128) k_event_forward(DevScene S, SortedPaths P
 }
 
 // gradient, per event: shadow-ray scatters -a l, local-estimate vertex
-// terms a h(x_b, mu_bd), and A_e = sum_d a for the per-path suffix sums
+// terms a h(x_b, mu_bd), and A_e = sum_d a for the per-path suffix sums.
+// The warp takes the cameras one at a time and walks its 32 shadow rays in
+// step.  Lanes holding events of one voxel are adjacent and their rays stay
+// together, so at each step the -a l terms of adjacent lanes in the same
+// voxel are summed (a segmented shuffle scan over runs of equal voxel ids,
+// 8 lanes deep) and one FP64 red per run (per 8 lanes of a longer run)
+// leaves the warp.
+__device__ __forceinline__ void red_runs(double* __restrict__ grad, int idx, float val, int lane) {
+    const unsigned full = 0xffffffffu;
+    const int prev = __shfl_up_sync(full, idx, 1);
+    const unsigned heads = __ballot_sync(full, lane == 0 || prev != idx);
+    if (heads == full) {                       // no lane shares its voxel
+        if (idx >= 0 && val != 0.0f) red_add(grad + idx, val);
+        return;
+    }
+    const int start = 31 - __clz(heads & ((2u << lane) - 1u));   // first lane of my run
+    const int chunk = start + ((lane - start) & ~7);               // first lane of my 8-lane chunk
+    float s = val;
+#pragma unroll
+    for (int d = 1; d < 8; d <<= 1) {
+        const float o = __shfl_up_sync(full, s, d);
+        if (lane - d >= chunk) s += o;
+    }
+    // the last lane of a run or of a chunk holds the chunk's sum
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u) || ((lane - start) & 7) == 7;
+    if (tail && idx >= 0 && s != 0.0f) red_add(grad + idx, s);
+}
+
 __global__ void __launch_bounds__(128) k_event_grad(DevScene S, SortedPaths P, Events E,
                                                     const float* __restrict__ beta_t,
                                                     const double* __restrict__ dldi, double* __restrict__ grad,
                                                     const float* __restrict__ cache) {
     __shared__ DevCam cams[kMaxCams];
     load_cams(S, cams);
+    const int lane = threadIdx.x & 31;
     const uint64_t pos = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pos >= P.buckets->n_events) return;
-    const uint4 a4 = E.a[pos];
-    const float4 b4 = E.b[pos];
-    const uint32_t pv = a4.w;
-    if (!vox_ok(S, pv)) {
-        atomicOr(S.err, kErrRecord);
-        return;
+    bool ok = pos < P.buckets->n_events;
+    float3 x = make_float3(0.f, 0.f, 0.f), om = x;
+    uint32_t pv = 0;
+    int v = 0;
+    float bct = 0.0f;
+    if (ok) {
+        const uint4 a4 = E.a[pos];
+        const float4 b4 = E.b[pos];
+        pv = a4.w;
+        if (!vox_ok(S, pv)) {
+            atomicOr(S.err, kErrRecord);
+            ok = false;
+        } else {
+            x = xyz(a4);
+            om = make_float3(b4.x, b4.y, b4.z);
+            v = lin_vox(S, pv);
+            bct = __ldg(beta_t + v);
+        }
     }
-    const float3 x = xyz(a4), om = make_float3(b4.x, b4.y, b4.z);
-    const int v = lin_vox(S, pv);
-    const float bct = __ldg(beta_t + v);
+    const unsigned full = 0xffffffffu;
     float A = 0.0f, hv = 0.0f;
     for (int c = 0; c < S.n_cams; ++c) {
-        const float ev = cache[(uint64_t)c * E.cap + pos];
-        if (ev == 0.0f) continue;
-        const Proj q = project(cams[c], x);
-        if (q.pix < 0) continue;
-        const float a = (float)__ldg(dldi + cams[c].off + q.pix) * ev;
-        if (a == 0.0f) continue;
-        A += a;
-        hv += a * score_vertex(S, bct, dot3(om, q.dir));
-        scatter_ray(S, grad, x, q.dir, pv, __int_as_float(0x7f800000), a);
+        float a = 0.0f;
+        float3 dir = x;
+        if (ok) {
+            const float ev = cache[(uint64_t)c * E.cap + pos];
+            if (ev != 0.0f) {
+                const Proj q = project(cams[c], x);
+                if (q.pix >= 0) {
+                    a = (float)__ldg(dldi + cams[c].off + q.pix) * ev;
+                    dir = q.dir;
+                    A += a;
+                    if (a != 0.0f) hv += a * score_vertex(S, bct, dot3(om, q.dir));
+                }
+            }
+        }
+        bool live = a != 0.0f;
+        if (!__any_sync(full, live)) continue;
+        Dda r;
+        r.init(S, x, dir, pv, __int_as_float(0x7f800000));
+        while (__any_sync(full, live)) {
+            int idx = -1 - lane;   // never equal across lanes
+            float val = 0.0f;
+            if (live) {
+                const float tn = r.next();
+                idx = r.idx;
+                val = -a * r.seg(tn);
+                live = r.step(S, tn);
+            }
+            red_runs(grad, idx, val, lane);
+        }
     }
-    if (hv != 0.0f) red_add(grad + v, hv);
-    E.val[pos] = A;
+    if (ok) {
+        if (hv != 0.0f) red_add(grad + v, hv);
+        E.val[pos] = A;
+    }
 }
 
 unsigned blocks(uint64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }

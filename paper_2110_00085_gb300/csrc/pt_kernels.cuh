@@ -38,7 +38,8 @@ struct Events {
     uint32_t* cursor;  // per bin: exclusive offsets, then fill positions
     uint32_t* partial; // block sums of the scan
     uint32_t n_bins;
-    int bin_bits;      // Morton bits per axis
+    int bin_bits;      // Morton bits per axis (<= 8: at most 2^24 bins)
+    int bin_shift;     // voxel coordinates >> bin_shift give the bin coordinates
     uint64_t cap;      // event capacity
 };
 

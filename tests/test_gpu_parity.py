@@ -135,7 +135,25 @@ def test_gradient_cache_equals_recompute():
     dldi = img - 0.5 * img.mean()
     g1 = paths.grad(bt, dldi, cache=True)
     g2 = paths.grad(bt, dldi, cache=False)
-    assert torch.allclose(g1, g2, rtol=1e-6, atol=1e-9 * g2.abs().max().item())
+    # the event kernel pre-sums up to 8 same-voxel FP32 terms per warp step
+    # before its FP64 red (a few units of roundoff of those terms)
+    assert torch.allclose(g1, g2, rtol=1e-5, atol=1e-7 * g2.abs().max().item())
+
+
+def test_gradient_cache_equals_recompute_dense_events():
+    """Many events per voxel (tiny grid, many paths): warps hold long runs of
+    same-voxel events, so the per-step merging of their shadow-ray terms is
+    exercised across 8-lane chunk boundaries."""
+    sc = synth.small_scene(n=6, n_cams=4, px=8, peak=30.0, seed=13, n_paths=1 << 16)
+    scene = N.Scene(sc)
+    br, bt = t32(sc.beta_cloud), t32(_perturbed(sc.beta_cloud, 6))
+    paths = N.Paths(scene).store(br, sc.n_paths, sc.seed)
+    img = paths.reweight(bt, cache=True)
+    dldi = img - 0.4 * img.mean()
+    g1 = paths.grad(bt, dldi, cache=True)
+    g2 = paths.grad(bt, dldi, cache=False)
+    assert g2.abs().max().item() > 0
+    assert torch.allclose(g1, g2, rtol=1e-5, atol=1e-7 * g2.abs().max().item())
 
 
 # ------------------------------------------------------------ edge cases ---
