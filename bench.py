@@ -293,20 +293,25 @@ def run_native(args, ws, rank, local):
     pk, pk_src = peaks()
     seg_x = T["seg_cross"]
     shd_x = T["shadow_cross"]
-    # algorithmic operations per voxel crossing of the traversal (derivation
-    # in the design doc): face-distance minimum (2), segment length (1), optical
-    # depth or scatter FMA (1), next face distance (3), index step (1),
-    # termination and bounds tests (2)
-    ops_per_cross = 10.0
+    # The voxel traversal is bound by the ALU pipe (compares, selects,
+    # min/max, integer index updates; the FMA pipe carries the rest).  Its
+    # algorithmic ALU work per voxel crossing (derivation in the design doc):
+    # next face = min of three (2), clipped segment length (2), end test (1),
+    # axis choice (3), per-axis counter selects (3), index step select and
+    # add (3), running t (1), bounds test (1) = 16 lane operations.
+    alu_per_cross = 16.0
     crosses = {"paths_reweight": shd_x + seg_x, "render_grad": shd_x + seg_x,
                "paths_store": seg_x}[dom]
-    achieved = ops_per_cross * crosses / (avg[dom] * 1e-3) / 1e12    # Top/s (FP32 lane ops)
+    achieved = alu_per_cross * crosses / (avg[dom] * 1e-3) / 1e12      # T ALU lane-ops/s
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    peak = 152 * 128 * sm_mhz * 1e6 / 1e12
-    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    peak = 152 * 64 * sm_mhz * 1e6 / 1e12   # 152 SMs x 4 partitions x 16 ALU lanes per clock
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Tops/s",
             "frac": achieved / peak, "traffic": None,
-            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({pk_src} max clock)",
-            "work": f"{ops_per_cross:.0f} FP32 ops per voxel crossing x {crosses:.3e} crossings per launch"}
+            "peak_source": f"derived: 152 SMs x 64 ALU-pipe lanes/clock x {sm_mhz:.0f} MHz ({pk_src} max SM clock)",
+            "work": f"{alu_per_cross:.0f} ALU ops per voxel crossing x {crosses:.3e} crossings per call",
+            "per_call_ms": {k: round(v, 3) for k, v in avg.items()},
+            "alu_frac_by_call": {k: round(alu_per_cross * (shd_x + seg_x if k != "paths_store" else seg_x)
+                                          / (v * 1e-3) / 1e12 / peak, 4) for k, v in avg.items()}}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
