@@ -88,7 +88,7 @@ def lib():
             L.or_intervals.argtypes = [C.POINTER(ORScene), _dp, _dp, C.c_double, _i64p, _dp, C.c_int]
             L.or_intervals.restype = C.c_int
             L.or_render.argtypes = [C.POINTER(ORScene), _fp, _fp, C.c_uint64, C.c_uint64, C.c_double,
-                                    _dp, _dp, _dp, _dp, _dp, _dp, _u64p, C.c_int]
+                                    _dp, _dp, _dp, _dp, _dp, _dp, _dp, _u64p, C.c_int]
             L.or_render.restype = C.c_int
             L.or_path.argtypes = [C.POINTER(ORScene), _fp, C.c_uint64, _dp, _dp, _i64p, _dp, C.POINTER(C.c_int)]
             L.or_path.restype = C.c_int
@@ -157,18 +157,24 @@ def _grid(b):
 
 def render(sc, beta_ref, beta_t=None, first: int = 0, n=None, n_norm=None, dldi=None,
            grad_abs: bool = False, grad_cond: bool = False, tallies: bool = False, fingerprints: bool = False,
-           threads: int = 1, epoch: int = 0, scene_id: int = 0, seed=None):
+           threads: int = 1, epoch: int = 0, scene_id: int = 0, seed=None, image_cond: bool = False):
     """Paths [first, first+n) sampled under ``beta_ref``, evaluated under
     ``beta_t`` (default: the same grid).  Returns a dict with ``images``
     (float64, n_pixels), and when asked ``grad``/``grad_abs`` (float64,
-    n_voxels), ``grad_cond`` (per voxel, an error budget for float32
-    implementations: sum over its length terms of |dL/dI * contribution|
-    times the length's conditioning (1/|d_axis| per bounding face) times how
-    far a float32 computation of the ray's origin vertex may lie from the
-    float64 one -- a few units of roundoff of the coordinates, plus
-    u (tau + 1) / beta for a collision point, which is ill-conditioned
-    where the extinction is small),
-    ``tallies`` (dict) and ``fingerprints`` (uint64, n)."""
+    n_voxels), ``tallies`` (dict), ``fingerprints`` (uint64, n) and two error
+    budgets for float32 implementations of the same paths:
+    ``image_cond`` (per pixel) and ``grad_cond`` (per voxel).  Each is
+    measured by perturbation: every path is sampled again four times with
+    each computed vertex moved, in a random direction, by a float32 roundoff
+    of its coordinates (plus the roundoff of the optical depth accumulated to
+    a collision, over beta there), and 4x the largest change over the draws
+    of the path's contributions (pixel by pixel) or gradient terms (voxel by
+    voxel) is added, together with the roundoff of the crossing times along
+    each ray.
+    Budgets are large only where the geometry is ill-conditioned: a
+    collision in thin air just past cloud edges, a grazing crossing, a
+    near-tie of a pixel or voxel decision.
+    """
     L = lib()
     os_ = OScene(sc, epoch=epoch, scene_id=scene_id, seed=seed)
     n = int(sc.n_paths if n is None else n)
@@ -177,6 +183,9 @@ def render(sc, beta_ref, beta_t=None, first: int = 0, n=None, n_norm=None, dldi=
     bt = br if beta_t is None else _grid(beta_t)
     img = np.zeros(os_.n_pixels, dtype=np.float64)
     out = {"images": img}
+    ic = np.zeros(os_.n_pixels, dtype=np.float64) if image_cond else None
+    if ic is not None:
+        out["image_cond"] = ic
     g = ga = gc = dl = None
     if dldi is not None:
         dl = np.ascontiguousarray(np.asarray(dldi, dtype=np.float64).reshape(-1))
@@ -191,7 +200,7 @@ def render(sc, beta_ref, beta_t=None, first: int = 0, n=None, n_norm=None, dldi=
     tal = np.zeros(L.or_tally_count(), dtype=np.float64) if tallies else None
     fp = np.zeros(n, dtype=np.uint64) if fingerprints else None
     rc = L.or_render(os_.ref, _ptr(br, _fp), _ptr(bt, _fp), C.c_uint64(first), C.c_uint64(n),
-                     C.c_double(n_norm), _ptr(img, _dp), _ptr(dl, _dp), _ptr(g, _dp), _ptr(ga, _dp),
+                     C.c_double(n_norm), _ptr(img, _dp), _ptr(ic, _dp), _ptr(dl, _dp), _ptr(g, _dp), _ptr(ga, _dp),
                      _ptr(gc, _dp), _ptr(tal, _dp), _ptr(fp, _u64p), int(threads))
     if rc != 0:
         raise RuntimeError(f"or_render failed ({rc})")

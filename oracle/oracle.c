@@ -124,6 +124,35 @@ static void draw(const or_scene* s, uint64_t path, uint32_t event, uint32_t tag,
     for (int i = 0; i < 4; ++i) u[i] = u01(w[i]);
 }
 
+/* ---- float32 error budget by perturbation (test infrastructure only) ----
+ * The images' budget for float32 implementations is measured, not bounded:
+ * each path is sampled again with every computed vertex moved by its
+ * float32 roundoff scale in a random direction (Monte Carlo arithmetic,
+ * Parker 1997), and the change of each event's contribution is recorded.
+ * The directions come from splitmix64 (Steele, Lea and Flood, OOPSLA 2014),
+ * independent of the method's Philox streams. */
+static uint64_t splitmix64(uint64_t x)
+{
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+/* unit vector, uniform on the sphere, for (path, vertex, draw) */
+static void pert_dir(uint64_t pid, int k, int r, double e[3])
+{
+    uint64_t h = splitmix64(pid ^ splitmix64(((uint64_t)(uint32_t)k << 32) | (uint32_t)r));
+    double a = (double)(h >> 40) / 16777216.0, b = (double)(splitmix64(h) >> 40) / 16777216.0;
+    double z = 2.0 * a - 1.0, q = sqrt(fmax(0.0, 1.0 - z * z)), ph = 2.0 * OR_PI * b;
+    e[0] = q * cos(ph); e[1] = q * sin(ph); e[2] = z;
+}
+
+#define OR_PERT_DRAWS 4     /* perturbed re-samplings per path */
+#define OR_PERT_SAFETY 4.0  /* budget = safety * max over draws of |change| */
+#define OR_PERT_ULPS 2.0    /* roundoffs per computed quantity */
+#define OR_U32 (1.0 / 16777216.0)   /* float32 unit roundoff, 2^-24 */
+
 /* FNV-1a, 64 bit, over the little-endian bytes of 32-bit words */
 static uint64_t fnv_word(uint64_t h, uint32_t w)
 {
@@ -454,8 +483,6 @@ typedef struct {
     double l[OR_MAXV];
     int64_t v[OR_MAXV];
     int type[OR_MAXV];       /* particle type chosen at x_k: 0 cloud, 1 air, 2 none */
-    double dpos[OR_MAXV];    /* error budget only: how far a float32 computation of
-                                x_k may sit from this float64 one (km) */
 } opath;
 
 typedef struct {
@@ -466,7 +493,16 @@ typedef struct {
     tcut* tb;
     ivl* iv2;
     tcut* tb2;
+    int64_t* touch;   /* budget only: voxels written by grad_add, when set */
+    int64_t ntouch, tcap;
 } octx;
+
+/* grad[v] += t, recording v in the touched list when one is attached */
+static void grad_add(octx* c, double* grad, int64_t v, double t)
+{
+    grad[v] += t;
+    if (c->touch && c->ntouch < c->tcap) c->touch[c->ntouch++] = v;
+}
 
 /*
  * Sample path `pid` under extinction bc (Secs. 3.4.1-3.4.2).
@@ -484,7 +520,7 @@ typedef struct {
  *    in the recycling ratio.
  * Tallies follow the physical weight for the energy-balance check.
  */
-static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double* tal)
+static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double* tal, int pert)
 {
     const or_scene* s = c->s;
     double u[4];
@@ -509,16 +545,22 @@ static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double
     P->v[0] = -1;
     P->l[0] = 0.0;
     P->type[0] = 2;
-    /* float32 position budget: unit roundoff u times the coordinate scale for
-     * every computed point, plus the collision point's sensitivity to the
-     * optical depth, u (tau + 1) / beta, where beta is small */
-    const double u32 = 1.0 / 16777216.0;
+    /* perturbed re-sampling only (error budget, pert > 0): every computed
+     * point moves by a float32 roundoff of the coordinate scale, a collision
+     * point also by the roundoff of the optical depth accumulated to it
+     * divided by beta there (large where beta is small): u (tau + 1) for the
+     * sampled depth, and for every face the flight crossed, its crossing
+     * time's roundoff u t_f times the jump of beta at that face */
     double Lsc = 0.0;
     for (int a = 0; a < 3; ++a) {
         const int na = a == 0 ? s->nx : a == 1 ? s->ny : s->nz;
         Lsc = fmax(Lsc, fabs(s->origin[a]) + na * s->voxel);
     }
-    P->dpos[0] = 8.0 * u32 * Lsc;
+    if (pert) {
+        double e[3];
+        pert_dir(pid, 0, pert, e);
+        for (int i = 0; i < 3; ++i) P->x[0][i] += OR_PERT_ULPS * OR_U32 * Lsc * e[i];
+    }
     double w = w0;
     double tau = -log(u[2]);
     for (int k = 1;; ++k) {
@@ -528,9 +570,14 @@ static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double
         int hit = 0;
         double tcol = 0.0;
         int64_t vcol = -1;
+        /* budget only: sum of t_f |beta jump| over the faces before the
+         * collision (start included) */
+        double jumps = 0.0, bprev = 0.0;
         for (int i = 0; i < n; ++i) {
             double bt = beta_tot(s, bc, c->iv[i].v);
             double len = c->iv[i].t1 - c->iv[i].t0;
+            jumps += fabs(bt - bprev) * c->iv[i].t0;
+            bprev = bt;
             if (tal) tal[T_SEG_CROSS] += 1.0;
             if (bt > 0.0 && tau - acc <= bt * len) {
                 tcol = c->iv[i].t0 + (tau - acc) / bt;
@@ -550,7 +597,12 @@ static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double
         P->v[k] = vcol;
         P->type[k] = 2;
         P->B = k;
-        P->dpos[k] = P->dpos[k - 1] + 8.0 * u32 * Lsc + 4.0 * u32 * (tau + 1.0) / beta_tot(s, bc, vcol);
+        if (pert) {
+            double e[3];
+            pert_dir(pid, k, pert, e);
+            double m = OR_PERT_ULPS * OR_U32 * (Lsc + (tau + 1.0 + jumps) / beta_tot(s, bc, vcol));
+            for (int i = 0; i < 3; ++i) P->x[k][i] += m * e[i];
+        }
         double bcv = (double)bc[vcol];
         double alb = beta_s(s, bcv) / beta_tot(s, bc, vcol);
         if (tal) { tal[T_COLLISIONS] += 1.0; tal[T_ABSORBED] += w * (1.0 - alb); }
@@ -620,19 +672,32 @@ static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double
  * sub-path.  Events with zero contribution are skipped (their score may be
  * infinite where beta_c = 0 and there is no air).
  */
-/* conditioning of an interval's length: how far its ends move along the
- * ray per unit displacement of the ray normal to the faces that bound it
- * (1 / |d_axis| per face end, 1 per segment end) */
-static double length_cond(const ivl* iv, const double d[3])
+/* float32 error budget of an interval's length: a float32 traversal
+ * computes each crossing time t with an error of a few units of roundoff of
+ * t itself (budget only, not part of the method) */
+static double time_roundoff(const ivl* iv)
 {
-    double k0 = iv->a0 >= 0 ? 1.0 / fabs(d[iv->a0]) : 1.0;
-    double k1 = iv->a1 >= 0 ? 1.0 / fabs(d[iv->a1]) : 1.0;
-    return k0 + k1;
+    return 4.0 * OR_U32 * (fabs(iv->t0) + fabs(iv->t1));
+}
+
+/* the same for an optical depth: sum_i x_i (t1 - t0) with x_i the total
+ * extinction under ba (minus that under bb when given); each face trades the
+ * jump of x there over its crossing time's roundoff */
+static double depth_roundoff(const or_scene* s, const float* ba, const float* bb, const ivl* iv, int n)
+{
+    double prev = 0.0, own = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double x = beta_tot(s, ba, iv[i].v) - (bb ? beta_tot(s, bb, iv[i].v) : 0.0);
+        own += fabs(x - prev) * fabs(iv[i].t0);
+        prev = x;
+    }
+    if (n > 0) own += fabs(prev) * fabs(iv[n - 1].t1);
+    return 4.0 * OR_U32 * own;
 }
 
 static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
-                      double inv_norm, double* img, const double* dldi,
-                      double* grad, double* gabs, double* gcond, double* tal, uint64_t* fp)
+                      double inv_norm, double* img, double* icond, int64_t* egp, double* eval,
+                      const double* dldi, double* grad, double* gabs, double* gcond, double* tal, uint64_t* fp)
 {
     const or_scene* s = c->s;
     /* fingerprint words: per event (voxel, pixel per camera, particle type),
@@ -647,9 +712,12 @@ static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
     double w0 = s->sun_irradiance * c->sun.area;
     double log_tr = 0.0;       /* sum over flights of tau_ref - tau_t */
     double vert = 1.0;         /* product of the vertex ratios k < b  */
+    double tr_cond = 0.0;      /* error budget of log_tr (float32 vertices) */
     for (int b = 1; b <= P->B; ++b) {
         int n = intervals(s, P->x[b - 1], P->om[b - 1], P->l[b], c->iv, c->tb);
         log_tr += optical_depth(s, br, c->iv, n) - optical_depth(s, bt, c->iv, n);
+        if (icond && br != bt)
+            tr_cond += depth_roundoff(s, br, bt, c->iv, n);
         if (b >= 2) {
             int64_t vk = P->v[b - 1];
             double mu = dot3(P->om[b - 2], P->om[b - 1]);
@@ -672,6 +740,7 @@ static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
             int col, row;
             int64_t pix = project(k, P->x[b], &col, &row);
             h = fnv_word(h, (uint32_t)(int32_t)pix);
+            if (egp) { egp[(b - 1) * s->n_cams + d] = pix < 0 ? -1 : k->off + pix; eval[(b - 1) * s->n_cams + d] = 0.0; }
             if (pix < 0) continue;
             double to[3] = {k->C[0] - P->x[b][0], k->C[1] - P->x[b][1], k->C[2] - P->x[b][2]};
             double r2 = dot3(to, to);
@@ -685,6 +754,10 @@ static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
             if (tal) { tal[T_IN_VIEW] += 1.0; tal[T_SHADOW_CROSS] += (double)ns; }
             int64_t gp = k->off + pix;
             if (img) img[gp] += ev * inv_norm;
+            if (eval) eval[(b - 1) * s->n_cams + d] = ev * inv_norm;
+            /* the shadow ray's and the flights' own float32 crossing times;
+             * the vertices' roundoff is measured by perturbation (or_render) */
+            if (icond) icond[gp] += fabs(ev * inv_norm) * (depth_roundoff(s, bt, NULL, c->iv2, ns) + tr_cond);
             if (!dldi || ev == 0.0) continue;
             double A = dldi[gp] * ev * inv_norm;
             /* flights 1..b */
@@ -692,32 +765,30 @@ static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
                 int nj = intervals(s, P->x[j - 1], P->om[j - 1], P->l[j], c->iv, c->tb);
                 for (int i = 0; i < nj; ++i) {
                     double t = A * (c->iv[i].t1 - c->iv[i].t0);
-                    grad[c->iv[i].v] -= t;
+                    grad_add(c, grad, c->iv[i].v, -t);
                     if (gabs) gabs[c->iv[i].v] += fabs(t);
-                    if (gcond)
-                        gcond[c->iv[i].v] += fabs(A) * length_cond(&c->iv[i], P->om[j - 1]) *
-                                             fmax(P->dpos[j - 1], P->dpos[j]);
+                    if (gcond) gcond[c->iv[i].v] += fabs(A) * time_roundoff(&c->iv[i]);
                 }
             }
             /* shadow ray x_b -> camera */
             for (int i = 0; i < ns; ++i) {
                 double t = A * (c->iv2[i].t1 - c->iv2[i].t0);
-                grad[c->iv2[i].v] -= t;
+                grad_add(c, grad, c->iv2[i].v, -t);
                 if (gabs) gabs[c->iv2[i].v] += fabs(t);
-                if (gcond) gcond[c->iv2[i].v] += fabs(A) * length_cond(&c->iv2[i], dir) * P->dpos[b];
+                if (gcond) gcond[c->iv2[i].v] += fabs(A) * time_roundoff(&c->iv2[i]);
             }
             /* scattering vertices 1..b-1 (angle between sampled directions) */
             for (int j = 1; j < b; ++j) {
                 int64_t vj = P->v[j];
                 double muj = dot3(P->om[j - 1], P->om[j]);
                 double t = A * s->albedo_cloud * or_phase_hg(s->hg_g, muj) / fs_medium(s, (double)bt[vj], muj);
-                grad[vj] += t;
+                grad_add(c, grad, vj, t);
                 if (gabs) gabs[vj] += fabs(t);
             }
             /* vertex b toward the camera */
             {
                 double t = A * s->albedo_cloud * or_phase_hg(s->hg_g, mu) / fs_medium(s, (double)bt[vb], mu);
-                grad[vb] += t;
+                grad_add(c, grad, vb, t);
                 if (gabs) gabs[vb] += fabs(t);
             }
         }
@@ -747,7 +818,7 @@ static int64_t total_pixels(const or_scene* s)
  */
 int or_render(const or_scene* s, const float* beta_ref, const float* beta_t,
               uint64_t first_path, uint64_t n_paths, double n_norm,
-              double* images, const double* dldi, double* grad, double* gabs,
+              double* images, double* icond, const double* dldi, double* grad, double* gabs,
               double* gcond, double* tallies, uint64_t* fingerprints, int threads)
 {
     if (s->max_orders + 1 >= OR_MAXV || s->max_orders < 1) return -1;
@@ -770,6 +841,8 @@ int or_render(const or_scene* s, const float* beta_ref, const float* beta_t,
 #endif
         octx c;
         c.s = s;
+        c.touch = NULL;
+        c.ntouch = c.tcap = 0;
         setup_sun(s, &c.sun);
         c.cams = (ocam*)malloc(sizeof(ocam) * (size_t)(s->n_cams > 0 ? s->n_cams : 1));
         setup_cams(s, c.cams);
@@ -780,6 +853,7 @@ int or_render(const or_scene* s, const float* beta_ref, const float* beta_t,
         c.tb2 = (tcut*)malloc(sizeof(tcut) * (size_t)mi);
         opath* P = (opath*)malloc(sizeof(opath));
         double* img = images;
+        double* ic = icond;
         double* g = grad;
         double* ga = gabs;
         double* gc = gcond;
@@ -787,29 +861,118 @@ int or_render(const or_scene* s, const float* beta_ref, const float* beta_t,
         memset(tal, 0, sizeof(tal));
         if (nt > 1) {
             img = images ? (double*)calloc((size_t)npix, sizeof(double)) : NULL;
+            ic = icond ? (double*)calloc((size_t)npix, sizeof(double)) : NULL;
             g = grad ? (double*)calloc((size_t)nvox, sizeof(double)) : NULL;
             ga = gabs ? (double*)calloc((size_t)nvox, sizeof(double)) : NULL;
             gc = gcond ? (double*)calloc((size_t)nvox, sizeof(double)) : NULL;
         }
+        /* per-event contributions (events b = 1..max_orders, camera d) of
+         * the path and of its perturbed re-samplings, for the image budget */
+        const int nev = s->max_orders * s->n_cams;
+        int64_t* egp0 = NULL; int64_t* egp1 = NULL;
+        double* ev0 = NULL; double* ev1 = NULL; double* dm = NULL;
+        if (ic) {
+            dm = (double*)malloc(sizeof(double) * (size_t)(nev > 0 ? nev : 1));
+            egp0 = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nev > 0 ? nev : 1));
+            egp1 = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nev > 0 ? nev : 1));
+            ev0 = (double*)malloc(sizeof(double) * (size_t)(nev > 0 ? nev : 1));
+            ev1 = (double*)malloc(sizeof(double) * (size_t)(nev > 0 ? nev : 1));
+        }
+        /* the path's own gradient terms, unperturbed and perturbed, with the
+         * voxels each evaluation wrote, for the gradient budget */
+        const int want_g = gc != NULL && dldi != NULL && g != NULL;
+        double* gp0 = NULL; double* gp1 = NULL; double* gmax = NULL;
+        int64_t* mark = NULL; int64_t* t0 = NULL; int64_t* t1 = NULL; int64_t* un = NULL;
+        const int64_t tcap = (int64_t)s->max_orders * s->n_cams *
+                             ((int64_t)(s->max_orders + 2) * mi + s->max_orders + 1);
+        if (want_g) {
+            gp0 = (double*)calloc((size_t)nvox, sizeof(double));
+            gp1 = (double*)calloc((size_t)nvox, sizeof(double));
+            gmax = (double*)calloc((size_t)nvox, sizeof(double));
+            mark = (int64_t*)calloc((size_t)nvox, sizeof(int64_t));
+            un = (int64_t*)malloc(sizeof(int64_t) * (size_t)(tcap > 0 ? tcap : 1) * (OR_PERT_DRAWS + 1));
+            t0 = (int64_t*)malloc(sizeof(int64_t) * (size_t)(tcap > 0 ? tcap : 1));
+            t1 = (int64_t*)malloc(sizeof(int64_t) * (size_t)(tcap > 0 ? tcap : 1));
+        }
+        int64_t stamp = 0;
+        int overflow = 0;
         for (uint64_t i = (uint64_t)tid; i < n_paths; i += (uint64_t)nt) {
             uint64_t pid = first_path + i;
-            sample_path(&c, beta_ref, pid, P, tal);
-            eval_path(&c, beta_ref, beta_t, P, inv_norm, img, dldi, g, ga, gc, tal,
+            if (ic) for (int j = 0; j < nev; ++j) { egp0[j] = -1; ev0[j] = 0.0; }
+            sample_path(&c, beta_ref, pid, P, tal, 0);
+            eval_path(&c, beta_ref, beta_t, P, inv_norm, img, ic, egp0, ev0, dldi, g, ga, gc, tal,
                       fingerprints ? &fingerprints[i] : NULL);
+            if (!ic && !want_g) continue;
+            int64_t n0 = 0;
+            if (want_g) {
+                c.touch = t0; c.ntouch = 0; c.tcap = tcap;
+                eval_path(&c, beta_ref, beta_t, P, inv_norm, NULL, NULL, NULL, NULL, dldi, gp0, NULL, NULL, NULL,
+                          NULL);
+                n0 = c.ntouch;
+                c.touch = NULL;
+                if (n0 >= tcap) overflow = 1;
+            }
+            /* an event that stays on its pixel adds the largest change of its
+             * contribution over the draws; one that moves (a near-tie of a
+             * discrete decision) adds its whole contribution on both pixels;
+             * a voxel adds the largest change of the path's gradient terms */
+            const double k = OR_PERT_SAFETY;
+            int64_t nun = 0;
+            ++stamp;
+            if (ic) for (int j = 0; j < nev; ++j) dm[j] = 0.0;
+            for (int r = 1; r <= OR_PERT_DRAWS; ++r) {
+                if (ic) for (int j = 0; j < nev; ++j) { egp1[j] = -1; ev1[j] = 0.0; }
+                sample_path(&c, beta_ref, pid, P, NULL, r);
+                if (want_g) { c.touch = t1; c.ntouch = 0; c.tcap = tcap; }
+                eval_path(&c, beta_ref, beta_t, P, inv_norm, NULL, NULL, ic ? egp1 : NULL, ic ? ev1 : NULL,
+                          want_g ? dldi : NULL, want_g ? gp1 : NULL, NULL, NULL, NULL, NULL);
+                const int64_t n1 = want_g ? c.ntouch : 0;
+                c.touch = NULL;
+                if (ic) {
+                    for (int j = 0; j < nev; ++j) {
+                        if (egp0[j] == egp1[j]) {
+                            dm[j] = fmax(dm[j], fabs(ev1[j] - ev0[j]));
+                        } else {
+                            if (egp0[j] >= 0) ic[egp0[j]] += k * fabs(ev0[j]) / OR_PERT_DRAWS;
+                            if (egp1[j] >= 0) ic[egp1[j]] += k * fabs(ev1[j]) / OR_PERT_DRAWS;
+                        }
+                    }
+                }
+                if (want_g) {
+                    if (n1 >= tcap) overflow = 1;
+                    for (int64_t j = 0; j < n0 + n1; ++j) {
+                        int64_t v = j < n0 ? t0[j] : t1[j - n0];
+                        if (mark[v] != stamp) { mark[v] = stamp; un[nun++] = v; }
+                        gmax[v] = fmax(gmax[v], fabs(gp1[v] - gp0[v]));
+                    }
+                    for (int64_t j = 0; j < n1; ++j) gp1[t1[j]] = 0.0;
+                }
+            }
+            if (ic)
+                for (int j = 0; j < nev; ++j)
+                    if (egp0[j] >= 0) ic[egp0[j]] += k * dm[j];
+            if (want_g) {
+                for (int64_t j = 0; j < nun; ++j) { gc[un[j]] += k * gmax[un[j]]; gmax[un[j]] = 0.0; }
+                for (int64_t j = 0; j < n0; ++j) gp0[t0[j]] = 0.0;
+            }
         }
+        free(egp0); free(egp1); free(ev0); free(ev1); free(dm);
+        free(gp0); free(gp1); free(gmax); free(mark); free(t0); free(t1); free(un);
 #ifdef _OPENMP
 #pragma omp critical
 #endif
         {
             if (nt > 1) {
                 if (img) for (int64_t j = 0; j < npix; ++j) images[j] += img[j];
+                if (ic) for (int64_t j = 0; j < npix; ++j) icond[j] += ic[j];
                 if (g) for (int64_t j = 0; j < nvox; ++j) grad[j] += g[j];
                 if (ga) for (int64_t j = 0; j < nvox; ++j) gabs[j] += ga[j];
                 if (gc) for (int64_t j = 0; j < nvox; ++j) gcond[j] += gc[j];
             }
             if (tallies) for (int j = 0; j < T_COUNT; ++j) tallies[j] += tal[j];
+            if (overflow) err = -2;
         }
-        if (nt > 1) { free(img); free(g); free(ga); free(gc); }
+        if (nt > 1) { free(img); free(ic); free(g); free(ga); free(gc); }
         free(P); free(c.iv); free(c.tb); free(c.iv2); free(c.tb2); free(c.cams);
     }
     return err;
@@ -820,13 +983,15 @@ int or_path(const or_scene* s, const float* beta, uint64_t pid, double* x, doubl
 {
     octx c;
     c.s = s;
+    c.touch = NULL;
+    c.ntouch = c.tcap = 0;
     setup_sun(s, &c.sun);
     int mi = max_intervals(s);
     c.cams = NULL;
     c.iv = (ivl*)malloc(sizeof(ivl) * (size_t)mi);
     c.tb = (tcut*)malloc(sizeof(tcut) * (size_t)mi);
     opath* P = (opath*)malloc(sizeof(opath));
-    sample_path(&c, beta, pid, P, NULL);
+    sample_path(&c, beta, pid, P, NULL, 0);
     int B = P->entered ? P->B : -1;
     for (int k = 0; k <= P->B && P->entered; ++k) {
         for (int i = 0; i < 3; ++i) { x[3 * k + i] = P->x[k][i]; om[3 * k + i] = P->om[k][i]; }

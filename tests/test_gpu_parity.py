@@ -36,9 +36,9 @@ def test_forward_matches_oracle(cfg, n, first):
     """Plain path tracing (Alg. 1 forward): 2^14 paths (many tiles) and a
     ragged count at an offset path id; workload 2 has air (two types)."""
     sc = synth.config(cfg, n_paths=n)
-    gi, oi, tg, to, nd = forward_parity(sc, sc.beta_cloud, n, first=first)
+    gi, oi, tg, to, nd, ic = forward_parity(sc, sc.beta_cloud, n, first=first)
     assert np.abs(oi).max() > 0
-    assert_images_close(gi, oi)
+    assert_images_close(gi, oi, cond=ic)
     # tallies: collision and path counts are integers; weights FP32-summed
     names = N.TALLY_NAMES
     for k in ("entered", "collisions"):
@@ -77,7 +77,8 @@ def test_recycled_forward_matches_oracle(cfg, n):
     sc = synth.config(cfg, n_paths=n)
     bt = _perturbed(sc.beta_cloud, seed=cfg)
     out = recycled_parity(sc, sc.beta_cloud, bt, n)
-    assert_images_close(out["gpu_images"], out["oracle_images"], what="recycled images")
+    assert_images_close(out["gpu_images"], out["oracle_images"], what="recycled images",
+                        cond=out["oracle_image_cond"])
 
 
 def test_recycling_ratio_is_one_at_reference():
@@ -172,8 +173,8 @@ def test_empty_medium_gives_zero():
 
 def test_single_path_and_first_order_only():
     sc = synth.config(1, n_paths=1).replace(max_orders=1)
-    gi, oi, *_ = forward_parity(sc, sc.beta_cloud, 64, first=777)
-    assert_images_close(gi, oi)
+    gi, oi, *_, ic = forward_parity(sc, sc.beta_cloud, 64, first=777)
+    assert_images_close(gi, oi, cond=ic)
 
 
 def test_invalid_arguments_raise():

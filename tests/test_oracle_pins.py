@@ -411,3 +411,31 @@ def test_fingerprints_identify_paths():
     # paths that never collide share one fingerprint; the rest are distinct
     assert np.mean(f1 != f3) > 0.25
     assert len(np.unique(f1)) > 0.25 * len(f1)
+
+
+# ------------------------------------------------ float32 image budget ------
+def test_image_budget_is_measured_not_injected():
+    """image_cond (the parity tolerance's float32 term) is test
+    infrastructure: asking for it leaves the images untouched, it is
+    non-negative and does not depend on the thread split, it is small where
+    the geometry is smooth (blob cloud, no air), and it is large for a path
+    whose last collision lies in thin air just past cloud edges (perturbing
+    its vertices by a float32 roundoff moves the collision far)."""
+    sc = synth.config(1, n_paths=1 << 10)
+    plain = O.render(sc, sc.beta_cloud)
+    r1 = O.render(sc, sc.beta_cloud, image_cond=True)
+    r4 = O.render(sc, sc.beta_cloud, image_cond=True, threads=4)
+    assert np.array_equal(plain["images"], r1["images"])
+    ic, im = r1["image_cond"], r1["images"]
+    assert (ic >= 0).all()
+    assert np.allclose(ic, r4["image_cond"], rtol=1e-12, atol=1e-300)
+    lit = im > 0
+    assert lit.sum() > 100
+    assert np.median(ic[lit] / im[lit]) < 1e-5
+    # thresholded cloud with air: one path with a thin-air last collision
+    c = synth.config(2, n_paths=1 << 11).replace(cameras=synth.arc_cameras(7, (1.28,) * 3, 40, 40))
+    br = c.beta_cloud.astype(np.float32)
+    one = O.render(c, br, first=718, n=1, n_norm=2048, image_cond=True, scene_id=2)
+    k = 2 * 40 * 40 + 788      # camera 2: the local estimate of its 4th collision
+    assert one["images"][k] > 0
+    assert one["image_cond"][k] > 100 * np.median(ic[lit] / im[lit]) * one["images"][k]
