@@ -194,12 +194,74 @@ int adam_step(float* beta, float* m, float* v, const double* grad, int64_t n,
               int32_t t, float lr, float b1, float b2, float eps, void* stream);
 
 /*
+ * adam_step_counted -- adam_step with the step number kept on the device:
+ * *step (device int32, start at 0) is incremented, then used for the bias
+ * corrections (written to scratch, device float[2]).  One captured CUDA
+ * graph can so replay every step.
+ */
+int adam_step_counted(float* beta, float* m, float* v, const double* grad, int64_t n,
+                      int32_t* step, float* scratch, float lr, float b1, float b2, float eps,
+                      void* stream);
+
+/*
  * loss_residual -- dL_dI = images - gt and *loss = 1/2 sum (images - gt)^2
  * (Eq. appearance_loss).  All device float64; loss is one double, written
  * (not accumulated).
  */
 int loss_residual(const double* images, const double* gt, int64_t n,
                   double* dL_dI, double* loss, void* stream);
+
+/*
+ * Batches: many scenes (each with its own grid size, cameras and stored
+ * paths) run each pass in one persistent launch.  Resident blocks pull
+ * (scene, tile) work items from a device counter (tiles of 128 paths, 128
+ * events or 1024 voxels), so scenes of uneven size share the GPU without a
+ * launch per scene.  The passes are those of paths_reweight(PT_CACHE) and
+ * render_grad(PT_CACHE), with the same results per scene.
+ *   batch_create : groups stored-path handles (owned by the caller, which
+ *                  must outlive the batch); sizes the persistent grid from
+ *                  the occupancy of the batched kernels.
+ *   batch_bind   : host arrays of n device pointers per scene: beta_t
+ *                  (grid), images (output), dL_dI (images layout), grad
+ *                  (grid, FP64).  Allocates missing contribution caches
+ *                  (synchronises).  Bind again after a paths_store that grew
+ *                  a handle.
+ *   batch_reweight, batch_grad : as paths_reweight / render_grad for every
+ *                  scene (outputs zeroed unless PT_ACCUMULATE); batch_grad
+ *                  requires PT_CACHE and a preceding batch_reweight(PT_CACHE).
+ *                  No allocation or synchronisation: capturable in a CUDA
+ *                  graph once bound.
+ *   batch_set_launch : launch shape (autotuning knobs).  reg_cap 0 runs the
+ *                  kernels with the compiler's register allocation, 1 the
+ *                  ones compiled for 10 resident blocks of 128 threads per
+ *                  SM for the event forward pass and 9 for the path-weight
+ *                  and event-gradient passes (as the single-scene kernels
+ *                  reach; a few registers spilled).  blocks_per_sm >= 1
+ *                  selects the persistent schedule with that many resident
+ *                  blocks per SM (clamped to the variant's occupancy);
+ *                  blocks_per_sm = 0 the grouped schedule: one block per
+ *                  tile of every scene (tiles laid out from the stored path
+ *                  count and event capacity), scene descriptors passed as a
+ *                  kernel parameter, up to 64 scenes per launch;
+ *                  blocks_per_sm = -1 the per-scene sequence: the launches
+ *                  of paths_reweight / render_grad, scene after scene (best
+ *                  when every scene fills the GPU on its own).  Results
+ *                  do not depend on the shape except for the order of the
+ *                  FP64 additions (and, across reg_cap variants, FP32
+ *                  rounding of single contributions).  Default: persistent,
+ *                  reg_cap 0, the occupancy limit.
+ *   batch_launch_limits : the occupancy limit (resident blocks per SM) of
+ *                  variant reg_cap.
+ */
+typedef struct pt_batch pt_batch;
+int batch_create(pt_paths* const* paths, int n, pt_batch** out);
+int batch_bind(pt_batch* batch, const float* const* beta_t, double* const* images,
+               const double* const* dL_dI, double* const* grad, void* stream);
+int batch_reweight(pt_batch* batch, uint32_t flags, void* stream);
+int batch_grad(pt_batch* batch, uint32_t flags, void* stream);
+int batch_set_launch(pt_batch* batch, int reg_cap, int blocks_per_sm);
+int batch_launch_limits(pt_batch* batch, int reg_cap, int* max_blocks_per_sm);
+int batch_free(pt_batch* batch);
 
 /*
  * render_forward_static -- render_forward for callers that cannot allocate

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "pt_kernels.cuh"
 
@@ -82,6 +83,29 @@ __global__ void k_resid(const double* __restrict__ img, const double* __restrict
 __global__ void k_adam(float* __restrict__ beta, float* __restrict__ m, float* __restrict__ v,
                        const double* __restrict__ g, int64_t n, float lr, float b1, float b2, float eps,
                        float inv_bc1, float inv_bc2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = __double2float_rn(g[i]);
+        const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
+        const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
+        m[i] = mi;
+        v[i] = vi;
+        const float step = lr * (mi * inv_bc1) / (sqrtf(vi * inv_bc2) + eps);
+        beta[i] = fmaxf(beta[i] - step, 0.0f);
+    }
+}
+
+// step counter on the device: t = ++(*step); bias corrections 1/(1 - b^t)
+__global__ void k_adam_count(int32_t* step, float b1, float b2, float* inv_bc) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int32_t t = ++(*step);
+    inv_bc[0] = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
+    inv_bc[1] = (float)(1.0 / (1.0 - pow((double)b2, (double)t)));
+}
+
+__global__ void k_adam_dev(float* __restrict__ beta, float* __restrict__ m, float* __restrict__ v,
+                           const double* __restrict__ g, int64_t n, float lr, float b1, float b2, float eps,
+                           const float* __restrict__ inv_bc) {
+    const float inv_bc1 = inv_bc[0], inv_bc2 = inv_bc[1];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float gi = __double2float_rn(g[i]);
         const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
@@ -510,6 +534,16 @@ int adam_step(float* beta, float* m, float* v, const double* grad, int64_t n, in
     return launch_status("adam_step");
 }
 
+int adam_step_counted(float* beta, float* m, float* v, const double* grad, int64_t n, int32_t* step,
+                      float* scratch, float lr, float b1, float b2, float eps, void* stream) {
+    if (!beta || !m || !v || !grad || !step || !scratch || n < 0)
+        return fail(PT_E_INVALID, "adam_step_counted: bad argument");
+    cudaStream_t st = S_(stream);
+    k_adam_count<<<1, 32, 0, st>>>(step, b1, b2, scratch);
+    if (n > 0) k_adam_dev<<<grid_for(n, 256), 256, 0, st>>>(beta, m, v, grad, n, lr, b1, b2, eps, scratch);
+    return launch_status("adam_step_counted");
+}
+
 int loss_residual(const double* images, const double* gt, int64_t n, double* dldi, double* loss, void* stream) {
     if (!images || !gt || !dldi || n < 0) return fail(PT_E_INVALID, "loss_residual: bad argument");
     cudaStream_t st = S_(stream);
@@ -517,6 +551,185 @@ int loss_residual(const double* images, const double* gt, int64_t n, double* dld
     if (n == 0) return PT_OK;
     k_resid<<<grid_for(n, 256, 152 * 4), 256, 0, st>>>(images, gt, n, dldi, loss);
     return launch_status("loss_residual");
+}
+
+// ------------------------------------------------------------ batches --
+}  // extern "C"
+
+struct pt_batch {
+    std::vector<pt_paths*> paths;
+    std::vector<BatchScene> host;
+    BatchScene* dev = nullptr;
+    BatchQueue q{};
+    int blocks = 0;    // resident blocks in all (persistent schedule)
+    int reg_cap = 0;
+    bool grouped = false;            // one block per tile, hardware-scheduled
+    bool sequence = false;           // the single-scene launches, scene by scene
+    std::vector<GroupTable> groups;  // grouped schedule: kGroupMax scenes per launch
+    bool bound = false;
+};
+
+namespace {
+int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(1, sms);
+}
+
+int ensure_cache(pt_paths* p, cudaStream_t st) {
+    const uint64_t need = p->ev.cap * (uint64_t)p->scene->ds.n_cams;
+    if (p->cache_cap >= need) return PT_OK;
+    PT_CUDA(cudaStreamSynchronize(st));
+    cudaFree(p->cache);
+    p->cache = nullptr;
+    p->bytes -= p->cache_cap * sizeof(float);
+    p->cache_cap = 0;
+    if (int rc = dev_alloc(&p->cache, need, &p->bytes, "contribution cache")) return rc;
+    p->cache_cap = need;
+    return PT_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int batch_create(pt_paths* const* paths, int n, pt_batch** out) {
+    if (!paths || !out || n < 1) return fail(PT_E_INVALID, "batch_create: need 1 or more stored-path handles");
+    *out = nullptr;
+    for (int s = 0; s < n; ++s)
+        if (!paths[s] || !paths[s]->scene || paths[s]->n == 0)
+            return fail(PT_E_INVALID, "batch_create: handle %d holds no stored paths", s);
+    pt_batch* b = new (std::nothrow) pt_batch();
+    if (!b) return fail(PT_E_OOM, "host allocation");
+    b->paths.assign(paths, paths + n);
+    b->host.resize(n);
+    int rc;
+    if ((rc = dev_alloc(&b->dev, (uint64_t)n, nullptr, "batch table")) ||
+        (rc = dev_alloc(&b->q.off, (uint64_t)kBatchPasses * (n + 1), nullptr, "batch tiles")) ||
+        (rc = dev_alloc(&b->q.counter, (uint64_t)kBatchPasses, nullptr, "batch counters"))) {
+        cudaFree(b->dev); cudaFree(b->q.off); cudaFree(b->q.counter);
+        delete b;
+        return rc;
+    }
+    b->blocks = sm_count() * batch_blocks_per_sm(0);
+    *out = b;
+    return PT_OK;
+}
+
+int batch_launch_limits(pt_batch* b, int reg_cap, int* max_blocks_per_sm) {
+    if (!b || !max_blocks_per_sm || (reg_cap != 0 && reg_cap != 1))
+        return fail(PT_E_INVALID, "batch_launch_limits: bad argument");
+    *max_blocks_per_sm = batch_blocks_per_sm(reg_cap);
+    return PT_OK;
+}
+
+int batch_set_launch(pt_batch* b, int reg_cap, int blocks_per_sm) {
+    if (!b || blocks_per_sm < -1 || (reg_cap != 0 && reg_cap != 1))
+        return fail(PT_E_INVALID, "batch_set_launch: bad argument");
+    b->reg_cap = reg_cap;
+    b->grouped = blocks_per_sm == 0;
+    b->sequence = blocks_per_sm == -1;
+    if (blocks_per_sm > 0) b->blocks = sm_count() * std::min(blocks_per_sm, batch_blocks_per_sm(reg_cap));
+    return PT_OK;
+}
+
+int batch_bind(pt_batch* b, const float* const* beta_t, double* const* images, const double* const* dldi,
+               double* const* grad, void* stream) {
+    if (!b || !beta_t || !images || !dldi || !grad) return fail(PT_E_INVALID, "batch_bind: null argument");
+    cudaStream_t st = S_(stream);
+    const int n = (int)b->paths.size();
+    for (int s = 0; s < n; ++s) {
+        pt_paths* p = b->paths[s];
+        if (!beta_t[s] || !images[s] || !dldi[s] || !grad[s])
+            return fail(PT_E_INVALID, "batch_bind: null buffer for scene %d", s);
+        if (int rc = ensure_cache(p, st)) return rc;
+        BatchScene& B = b->host[s];
+        B.S = p->scene->ds;
+        B.P = sorted_view(p);
+        B.E = p->ev;
+        B.beta_t = beta_t[s];
+        B.beta_ref = p->beta_ref;
+        B.dbeta = p->dbeta;
+        B.images = images[s];
+        B.dldi = dldi[s];
+        B.grad = grad[s];
+        B.cache = p->cache;
+        B.V = p->V;
+    }
+    // grouped schedule: kernel-parameter tables of up to kGroupMax scenes,
+    // blocks laid out from the scenes' upper bounds
+    b->groups.assign((size_t)((n + kGroupMax - 1) / kGroupMax), GroupTable{});
+    for (int s = 0; s < n; ++s) {
+        GroupTable& t = b->groups[(size_t)(s / kGroupMax)];
+        const int k = t.n++;
+        t.sc[k] = b->host[s];
+        uint32_t tiles[kGroupPasses];
+        group_tiles(b->host[s], tiles);
+        for (int p = 0; p < kGroupPasses; ++p) {
+            const uint64_t end = (uint64_t)t.off[p][k] + tiles[p];
+            if (end > 0x7fffffffull) return fail(PT_E_INVALID, "batch_bind: too many tiles in one group");
+            t.off[p][k + 1] = (uint32_t)end;
+        }
+    }
+    PT_CUDA(cudaMemcpyAsync(b->dev, b->host.data(), sizeof(BatchScene) * n, cudaMemcpyHostToDevice, st));
+    PT_CUDA(cudaStreamSynchronize(st));
+    b->bound = true;
+    return PT_OK;
+}
+
+int batch_reweight(pt_batch* b, uint32_t flags, void* stream) {
+    if (!b || !b->bound) return fail(PT_E_INVALID, "batch_reweight: batch not bound");
+    cudaStream_t st = S_(stream);
+    const int n = (int)b->paths.size();
+    if (!(flags & PT_ACCUMULATE))
+        for (int s = 0; s < n; ++s)
+            PT_CUDA(cudaMemsetAsync(b->host[s].images, 0, sizeof(double) * b->paths[s]->scene->n_pixels, st));
+    if (b->sequence) {
+        for (int s = 0; s < n; ++s) {
+            const BatchScene& B = b->host[s];
+            launch_delta(B.beta_t, B.beta_ref, B.dbeta, B.V, st);
+            launch_reweight(B.S, B.P, B.E, B.beta_t, B.beta_ref, B.dbeta, B.images,
+                            (flags & PT_CACHE) ? B.cache : nullptr, st);
+        }
+    } else if (b->grouped)
+        for (const GroupTable& t : b->groups) launch_group_reweight(t, (flags & PT_CACHE) != 0, b->reg_cap, st);
+    else
+        launch_batch_reweight(b->dev, n, b->q, (flags & PT_CACHE) != 0, b->reg_cap, b->blocks, st);
+    for (int s = 0; s < n; ++s) b->paths[s]->cache_valid = (flags & PT_CACHE) != 0;
+    return launch_status("batch_reweight");
+}
+
+int batch_grad(pt_batch* b, uint32_t flags, void* stream) {
+    if (!b || !b->bound) return fail(PT_E_INVALID, "batch_grad: batch not bound");
+    if (!(flags & PT_CACHE)) return fail(PT_E_INVALID, "batch_grad: the batched gradient reads the cache (PT_CACHE)");
+    const int n = (int)b->paths.size();
+    for (int s = 0; s < n; ++s)
+        if (!b->paths[s]->cache_valid)
+            return fail(PT_E_INVALID, "batch_grad: scene %d has no cache from batch_reweight(PT_CACHE)", s);
+    cudaStream_t st = S_(stream);
+    if (!(flags & PT_ACCUMULATE))
+        for (int s = 0; s < n; ++s)
+            PT_CUDA(cudaMemsetAsync(b->host[s].grad, 0, sizeof(double) * b->paths[s]->V, st));
+    if (b->sequence) {
+        for (int s = 0; s < n; ++s) {
+            const BatchScene& B = b->host[s];
+            launch_grad(B.S, B.P, B.E, B.beta_t, B.beta_ref, B.dbeta, B.dldi, B.grad, B.cache, st);
+        }
+    } else if (b->grouped)
+        for (const GroupTable& t : b->groups) launch_group_grad(t, b->reg_cap, st);
+    else
+        launch_batch_grad(b->dev, n, b->q, b->reg_cap, b->blocks, st);
+    return launch_status("batch_grad");
+}
+
+int batch_free(pt_batch* b) {
+    if (!b) return PT_OK;
+    cudaDeviceSynchronize();
+    cudaFree(b->dev);
+    cudaFree(b->q.off);
+    cudaFree(b->q.counter);
+    delete b;
+    return PT_OK;
 }
 
 int pt_check(const pt_scene* sc, void* stream) {

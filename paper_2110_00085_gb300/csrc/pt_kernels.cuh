@@ -108,6 +108,58 @@ void launch_grad(const DevScene& S, const SortedPaths& P, const Events& E, const
 
 void launch_delta(const float* a, const float* b, float* out, int64_t n, cudaStream_t st);
 
+// ------------------------------------------------------------ batches --
+// One scene of a batch: its constants, stored paths, events and the device
+// buffers bound for the current step.
+struct BatchScene {
+    DevScene S;
+    SortedPaths P;
+    Events E;
+    const float* beta_t;
+    const float* beta_ref;
+    float* dbeta;
+    double* images;
+    const double* dldi;
+    double* grad;
+    float* cache;
+    int64_t V;
+};
+
+// Work-queue state of a batch (device): per pass, tile offsets per scene
+// and the item counter.
+struct BatchQueue {
+    uint32_t* off;       // kBatchPasses x (n + 1)
+    uint32_t* counter;   // kBatchPasses
+};
+constexpr int kBatchPasses = 6;   // delta, path weights, event forward, event grad, path grad, (spare)
+
+// Grouped launches: one ordinary grid per pass over the tiles of up to
+// kGroupMax scenes, laid out from host-known upper bounds (stored paths,
+// event capacity, voxels).  The table travels as a kernel parameter, so a
+// block's scene (found from blockIdx) and every field of it are uniform
+// constant-bank reads, as in the single-scene kernels.
+constexpr int kGroupMax = 64;
+constexpr int kGroupPasses = 5;   // delta, path weights, event forward, event grad, path grad
+struct GroupTable {
+    int n;
+    uint32_t off[kGroupPasses][kGroupMax + 1];   // first block of each scene, per pass
+    BatchScene sc[kGroupMax];
+};
+static_assert(sizeof(GroupTable) <= 32000, "a group table must fit the kernel parameter space");
+// tiles of one scene for each pass (upper bounds)
+void group_tiles(const BatchScene& s, uint32_t tiles[kGroupPasses]);
+void launch_group_reweight(const GroupTable& t, bool cache, int reg_cap, cudaStream_t st);
+void launch_group_grad(const GroupTable& t, int reg_cap, cudaStream_t st);
+
+// persistent launches over all scenes: reweight = delta + path weights +
+// event forward; grad = event grad + path grad.  blocks = resident blocks;
+// reg_cap 1 selects the kernels compiled for 10 resident blocks per SM.
+void launch_batch_reweight(const BatchScene* scenes, int n, const BatchQueue& q, bool cache, int reg_cap, int blocks,
+                           cudaStream_t st);
+void launch_batch_grad(const BatchScene* scenes, int n, const BatchQueue& q, int reg_cap, int blocks,
+                       cudaStream_t st);
+int batch_blocks_per_sm(int reg_cap);   // occupancy of the slowest-filling pass
+
 // gradient without a contribution cache: per path, re-traces the shadow rays
 void launch_grad_reference(const DevScene& S, const SortedPaths& P, const float* beta_t, const float* beta_ref,
                            const float* dbeta, const double* dldi, double* grad, cudaStream_t st);

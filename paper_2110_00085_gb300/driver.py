@@ -17,8 +17,13 @@ import torch
 
 from . import native as N
 
-# kernels launched per call (for launch accounting)
-LAUNCHES = {"store": 5, "reweight": 2, "residual": 1, "grad_cache": 1, "grad": 2, "adam": 1}
+# kernels of this library launched per call (for launch accounting; memsets
+# are not counted): store = sample + 4 sort + 5 event-binning kernels,
+# reweight = delta + path weights + event forward, cached gradient = event
+# gradient + path gradient, uncached = delta + per-path gradient, counted
+# Adam = step counter + update (batched passes: native.Batch.kernels_per_step)
+LAUNCHES = {"store": 10, "reweight": 3, "residual": 1, "grad_cache": 2, "grad": 2, "adam": 1,
+            "adam_counted": 2}
 
 
 class Reconstruction:
@@ -74,4 +79,121 @@ class Reconstruction:
         N.adam_step(self.beta, self.m, self.v, self.grad, self.t + 1, self.lr, self.b1, self.b2, self.eps)
         self.launches += LAUNCHES["reweight"] + LAUNCHES["residual"] + LAUNCHES["adam"] + (
             LAUNCHES["grad_cache"] if self.cache else LAUNCHES["grad"])
+        self.t += 1
+
+
+class BatchReconstruction:
+    """Alg. 2 on many scenes at once: every pass of a step is one persistent
+    launch over all scenes (``native.Batch``).  The step after the optional
+    resample (reweight, residuals, gradient, Adam) has fixed buffers and a
+    device-side Adam step counter, so it can be captured once in a CUDA graph
+    and replayed every step."""
+
+    def __init__(self, scenes, gts, beta0s, n_paths, n_r: int = 10, lrs=None, seeds=None,
+                 b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+        self.scenes = list(scenes)
+        n = len(self.scenes)
+        self.gts = list(gts)
+        self.beta = [b.clone().contiguous() for b in beta0s]
+        self.m = [torch.zeros_like(b) for b in self.beta]
+        self.v = [torch.zeros_like(b) for b in self.beta]
+        dev = self.beta[0].device
+        self.steps = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in range(n)]
+        self.scratch = [torch.zeros(2, dtype=torch.float32, device=dev) for _ in range(n)]
+        self.n_paths = [int(k) for k in n_paths]
+        self.n_r = int(n_r)
+        self.lrs = list(lrs) if lrs is not None else [1.0] * n
+        self.seeds = list(seeds) if seeds is not None else [1234 + i for i in range(n)]
+        self.b1, self.b2, self.eps = b1, b2, eps
+        self.paths = [N.Paths(sc) for sc in self.scenes]
+        self.images = [sc.new_images() for sc in self.scenes]
+        self.dldi = [torch.zeros_like(im) for im in self.images]
+        self.grad = [torch.zeros(sc.n_voxels, dtype=torch.float64, device=dev) for sc in self.scenes]
+        self.loss = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in range(n)]
+        self.t = 0
+        self.epoch = 0
+        self.batch = None
+        self.graph = None
+        self.launches = 0
+
+    def resample(self):
+        for p, b, n, s in zip(self.paths, self.beta, self.n_paths, self.seeds):
+            p.store(b, n, s, epoch=self.epoch)
+        self.epoch += 1
+        if self.batch is None:
+            self.batch = N.Batch(self.paths)
+        self.batch.bind(self.beta, self.images, self.dldi, self.grad)
+        # the grouped schedule passes the scene table by value: a graph
+        # captured before this bind may hold stale descriptors
+        self.graph = None
+        self.launches += LAUNCHES["store"] * len(self.scenes)
+
+    def snapshot(self) -> dict:
+        """Optimisation state (extinction, Adam moments and step counters,
+        step and resample counters), for checkpoint / resume."""
+        return {"beta": [b.clone() for b in self.beta], "m": [x.clone() for x in self.m],
+                "v": [x.clone() for x in self.v], "steps": [x.clone() for x in self.steps],
+                "t": self.t, "epoch": self.epoch}
+
+    def restore(self, snap: dict):
+        """Back to a snapshot; tensors are copied in place (the bound batch
+        and any captured graph point at them).  From a snapshot taken at a
+        resample boundary (t mod N_r == 0) the next steps repeat exactly:
+        the resample draws the same paths (same seeds and epoch)."""
+        for name in ("beta", "m", "v", "steps"):
+            for dst, src in zip(getattr(self, name), snap[name]):
+                dst.copy_(src)
+        self.t = snap["t"]
+        self.epoch = snap["epoch"]
+        self.graph = None
+
+    def set_launch(self, reg_cap: int, blocks_per_sm: int):
+        """Launch shape of the batched passes (see native.Batch.set_launch);
+        the step graph is captured again with it."""
+        self.batch.set_launch(reg_cap, blocks_per_sm)
+        self.graph = None
+
+    def _body(self, batched: bool = True):
+        if batched:
+            self.batch.reweight(cache=True)
+        else:
+            for p, b, im in zip(self.paths, self.beta, self.images):
+                p.reweight(b, im, cache=True)
+        for im, gt, d, l in zip(self.images, self.gts, self.dldi, self.loss):
+            N.loss_residual(im, gt, d, l)
+        if batched:
+            self.batch.grad(cache=True)
+        else:
+            for p, b, d, g in zip(self.paths, self.beta, self.dldi, self.grad):
+                p.grad(b, d, g, cache=True)
+        for b, m, v, g, st, sc, lr in zip(self.beta, self.m, self.v, self.grad, self.steps, self.scratch, self.lrs):
+            N.adam_step_counted(b, m, v, g, st, sc, lr, self.b1, self.b2, self.eps)
+
+    def step(self, use_graph: bool = False, batched: bool = True):
+        """One Adam step on every scene.  ``batched=False`` issues the
+        per-scene calls one scene after another on the same state (the
+        comparison the batched launch is measured against)."""
+        if self.t % self.n_r == 0:
+            self.resample()
+        if not batched:
+            self._body(batched=False)
+            n = len(self.scenes)
+            self.launches += n * (LAUNCHES["reweight"] + LAUNCHES["residual"] + LAUNCHES["grad_cache"]
+                                  + LAUNCHES["adam_counted"])
+            self.t += 1
+            return
+        if use_graph:
+            if self.graph is None:
+                # capture after each resample / launch-shape change; buffers,
+                # the batch table and the Adam counters are fixed in between,
+                # so the same graph serves the steps until the next one
+                torch.cuda.synchronize()
+                self.graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(self.graph):
+                    self._body()
+            self.graph.replay()
+        else:
+            self._body()
+        n = len(self.scenes)
+        self.launches += n * (LAUNCHES["residual"] + LAUNCHES["adam_counted"]) + sum(self.batch.kernels_per_step())
         self.t += 1

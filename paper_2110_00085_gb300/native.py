@@ -81,9 +81,18 @@ def load():
         L.adam_step.argtypes = [_vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.c_float, C.c_float, C.c_float,
                                 C.c_float, _vp]
         L.loss_residual.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
+        L.adam_step_counted.argtypes = [_vp, _vp, _vp, _vp, C.c_int64, _vp, _vp, C.c_float, C.c_float, C.c_float,
+                                        C.c_float, _vp]
         L.pt_check.argtypes = [_vp, _vp]
         L.render_forward_static.argtypes = [C.POINTER(PtSceneDesc), _vp, _u64, _u64, C.c_double, _u64, _u32,
                                             _vp, _u32, _vp]
+        L.batch_create.argtypes = [C.POINTER(_vp), C.c_int, C.POINTER(_vp)]
+        L.batch_bind.argtypes = [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), _vp]
+        L.batch_reweight.argtypes = [_vp, _u32, _vp]
+        L.batch_grad.argtypes = [_vp, _u32, _vp]
+        L.batch_set_launch.argtypes = [_vp, C.c_int, C.c_int]
+        L.batch_launch_limits.argtypes = [_vp, C.c_int, C.POINTER(C.c_int)]
+        L.batch_free.argtypes = [_vp]
         L.pt_last_error.restype = C.c_char_p
         L.pt_version.restype = C.c_char_p
         _lib = L
@@ -269,6 +278,17 @@ def adam_step(beta, m, v, grad, t: int, lr: float, b1: float = 0.9, b2: float = 
     _check(rc, "adam_step")
 
 
+def adam_step_counted(beta, m, v, grad, step, scratch, lr: float, b1: float = 0.9, b2: float = 0.999,
+                      eps: float = 1e-8, stream=None):
+    """Adam with the step number in device memory (``step``: int32[1])."""
+    n = beta.numel()
+    rc = load().adam_step_counted(_dev(beta, torch.float32, "beta"), _dev(m, torch.float32, "m", n),
+                                  _dev(v, torch.float32, "v", n), _dev(grad, torch.float64, "grad", n), n,
+                                  _dev(step, torch.int32, "step", 1), _dev(scratch, torch.float32, "scratch", 2),
+                                  float(lr), float(b1), float(b2), float(eps), _vp(_stream(stream)))
+    _check(rc, "adam_step_counted")
+
+
 def loss_residual(images, gt, dldi=None, loss=None, stream=None):
     n = images.numel()
     if dldi is None:
@@ -329,3 +349,72 @@ def render_forward_static(sc, beta: torch.Tensor, n_paths: int, seed: int, first
                                       PT_ACCUMULATE if accumulate else 0, _vp(_stream(stream)))
     _check(rc, "render_forward_static")
     return images
+
+
+class Batch:
+    """Several stored-path handles run as one persistent launch per pass."""
+
+    def __init__(self, paths_list):
+        self.paths = list(paths_list)
+        arr = (_vp * len(self.paths))(*[p._h.value for p in self.paths])
+        h = _vp()
+        _check(load().batch_create(arr, len(self.paths), C.byref(h)), "batch_create")
+        self._h = h
+        self._bound = None
+        self.shape = (0, self.launch_limit(0))   # the library's default launch shape
+
+    def bind(self, betas, images, dldis, grads, stream=None):
+        n = len(self.paths)
+        def ptrs(ts, dtype, what, sizes):
+            return (_vp * n)(*[_dev(t, dtype, what, k) for t, k in zip(ts, sizes)])
+        vox = [p.scene.n_voxels for p in self.paths]
+        pix = [p.scene.n_pixels for p in self.paths]
+        args = (ptrs(betas, torch.float32, "beta_t", vox), ptrs(images, torch.float64, "images", pix),
+                ptrs(dldis, torch.float64, "dL_dI", pix), ptrs(grads, torch.float64, "grad", vox))
+        _check(load().batch_bind(self._h, *args, _vp(_stream(stream))), "batch_bind")
+        self._bound = (list(betas), list(images), list(dldis), list(grads))   # keep the tensors alive
+
+    def reweight(self, cache: bool = True, accumulate: bool = False, stream=None):
+        flags = (PT_CACHE if cache else 0) | (PT_ACCUMULATE if accumulate else 0)
+        _check(load().batch_reweight(self._h, flags, _vp(_stream(stream))), "batch_reweight")
+
+    def grad(self, cache: bool = True, accumulate: bool = False, stream=None):
+        flags = (PT_CACHE if cache else 0) | (PT_ACCUMULATE if accumulate else 0)
+        _check(load().batch_grad(self._h, flags, _vp(_stream(stream))), "batch_grad")
+
+    def set_launch(self, reg_cap: int, blocks_per_sm: int):
+        """Launch shape: register variant (0 compiler's, 1 capped for 10
+        blocks per SM) and resident blocks per SM of the persistent
+        schedule, or 0 for the grouped schedule (one block per tile), or -1
+        for the per-scene sequence."""
+        _check(load().batch_set_launch(self._h, int(reg_cap), int(blocks_per_sm)), "batch_set_launch")
+        self.shape = (int(reg_cap), int(blocks_per_sm))
+
+    def kernels_per_step(self) -> tuple:
+        """Kernels of this library launched by (reweight, grad) in the
+        current shape: per-scene sequence = 3 + 2 per scene, grouped = 3 + 2
+        per group of up to 64 scenes, persistent = tile offsets + 3 and tile
+        offsets + 2."""
+        if self.shape[1] == -1:
+            return 3 * len(self.paths), 2 * len(self.paths)
+        if self.shape[1] == 0:
+            g = (len(self.paths) + 63) // 64
+            return 3 * g, 2 * g
+        return 4, 3
+
+    def launch_limit(self, reg_cap: int) -> int:
+        """Occupancy limit (resident blocks per SM) of register variant reg_cap."""
+        m = C.c_int(0)
+        _check(load().batch_launch_limits(self._h, int(reg_cap), C.byref(m)), "batch_launch_limits")
+        return m.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().batch_free(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
