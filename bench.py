@@ -268,6 +268,58 @@ def run_batch(args, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def calibrate_matched(args, ws, scene, gt_img, beta0, n, lr, seed, reuse_ms):
+    """Resample budget of equal gradient error and its step time.
+
+    One recycling window is run after a first window (as in the timed
+    region), with an independent second path set giving the reuse error per
+    step; fresh-path errors are swept over budgets n/8 .. n at every
+    extinction of that window; n* solves e_resample(n*) = e_reuse (both RMS
+    over the window) on the fitted log-log line, and the Alg. 1 step is
+    timed at n* (capped at 2n)."""
+    import torch
+    from paper_2110_00085_gb300 import calibrate as CAL
+    from paper_2110_00085_gb300.driver import Reconstruction
+
+    rc = Reconstruction(scene, gt_img, beta0, n, n_r=N_R, lr=lr, seed=seed, cache=True)
+    for _ in range(N_R):
+        rc.step()
+    er = CAL.reuse_errors(rc, seed_b=seed + 7777)
+    rc.paths.close()
+    budgets = [n // 8, n // 4, n // 2, n]
+    # the same extinctions as the reuse errors: every step of the window
+    es, es2 = CAL.resample_errors_both(scene, gt_img, er["betas"], budgets)
+    fit = CAL.n_star(er["rms"], es)
+    fit2 = CAL.n_star(er["rms_l2"], es2)
+    n_star = int(min(max(round(fit["n_star"]), 1024), 2 * n))
+    res = Reconstruction(scene, gt_img, beta0, n_star, n_r=1, lr=lr, seed=seed, cache=True)
+    for _ in range(max(1, args.warmup)):
+        res.step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        res.step()
+    b.record()
+    torch.cuda.synchronize()
+    ms_star = max_over_ranks(ws, a.elapsed_time(b) / args.steps)
+    res.paths.close()
+    return {"window": f"Adam steps {N_R}-{2 * N_R - 1} (paths stored at step {N_R})",
+            "error": "L1 spread of two independent gradient estimates (mean over voxels of |g_a - g_b|), "
+                     "RMS over the window",
+            "e_reuse": er["rms"], "e_reuse_per_step": [float(f"{e:.5g}") for e in er["per_step"]],
+            "l2": {"e_reuse": er["rms_l2"], "e_resample": {str(k): v for k, v in es2.items()},
+                   "loglog_slope": fit2["slope"], "n_star_fit": fit2["n_star"],
+                   "signal_norm_mean": sum(er["signal"]) / len(er["signal"])},
+            "e_resample": {str(k): v for k, v in es.items()}, "loglog_slope": fit["slope"],
+            "n_star": n_star, "n_star_fit": fit["n_star"], "capped": fit["n_star"] > 2 * n,
+            "reuse_ms_per_step": reuse_ms, "resample_ms_per_step_at_n_star": ms_star,
+            "reuse_speedup": ms_star / reuse_ms,
+            "fresh_equivalent_paths_per_s": {"reuse": ws * n_star / (reuse_ms * 1e-3),
+                                             "resample": ws * n_star / (ms_star * 1e-3)}}
+
+
 def run_native(args, ws, rank, local):
     import numpy as np
     import torch
@@ -348,6 +400,11 @@ def run_native(args, ws, rank, local):
     ms_res = max_over_ranks(ws, r0.elapsed_time(r1) / args.steps)
     res.paths.close()
 
+    # ---- matched gradient error: reuse at n vs resample at n* ----
+    matched = None
+    if not args.no_calibration:
+        matched = calibrate_matched(args, ws, scene, gt_img, beta0, n, lr, sc.seed + rank, ms)
+
     # ---- end to end through the public API with host buffers ----
     gt_host = gt_img.cpu().pin_memory()
     loss_host = torch.zeros(1, dtype=torch.float64).pin_memory()
@@ -416,7 +473,8 @@ def run_native(args, ws, rank, local):
                    "stored_paths": int(info["n_stored"]), "records": int(info["n_records"]),
                    "mean_collisions": T["collisions"] / max(T["entered"], 1.0)},
         "resample": {"ms_per_step": ms_res, "value": ws * n / (ms_res * 1e-3), "unit": UNIT,
-                     "note": "Alg. 1 at the same path budget (error matching not applied)"},
+                     "note": "Alg. 1 at the same path budget"},
+        "matched_error": matched,
         "kernels_ms": {k: round(v, 3) for k, v in avg.items()},
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -438,6 +496,7 @@ def main():
     ap.add_argument("--paths", type=int, default=None, help="override the path budget (tests only)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-calibration", action="store_true", help="skip the matched-gradient-error arm")
     ap.add_argument("--workload", default="noise128", choices=["noise128", "batch"])
     ap.add_argument("--path-scale", type=int, default=0, help="batch workload: lower every 2^k path budget by k")
     args = ap.parse_args()
