@@ -427,6 +427,10 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
             --E.bin_bits;
             ++E.bin_shift;
         }
+        // spare bin bits order the events inside their voxel (up to 2 per axis):
+        // lanes of a warp then hold nearby events, whose shadow rays keep together
+        E.bin_sub = std::min(2, 8 - E.bin_bits);
+        E.bin_bits += E.bin_sub;
         E.n_bins = 1u << (3 * E.bin_bits);
         E.cap = n * (uint64_t)sc->ds.max_orders;
         if ((rc = dev_alloc(&E.a, E.cap, &by, "events A")) || (rc = dev_alloc(&E.b, E.cap, &by, "events B")) ||

@@ -98,19 +98,11 @@ __device__ __forceinline__ uint64_t fnv_word(uint64_t h, uint32_t w) {
 }
 constexpr uint64_t kFnvBasis = 0xcbf29ce484222325ull;
 
-// ------------------------------------------------- FP32 -> FP64 widening --
-// Exact widening of finite floats with integer operations only (no FP64
-// pipe, which is narrow on GB300): the magnitude bits shift into place and
-// the exponent bias moves from 127 to 1023.  Subnormal floats flush to zero;
-// the accumulated values are finite by construction.
-__device__ __forceinline__ double widen(float f) {
-    const uint32_t b = __float_as_uint(f);
-    const uint64_t mag = (((uint64_t)(b & 0x7fffffffu)) << 29) + (896ull << 52);
-    const uint64_t out = ((uint64_t)(b & 0x80000000u) << 32) | ((b & 0x7f800000u) ? mag : 0ull);
-    return __longlong_as_double((long long)out);
-}
-
-__device__ __forceinline__ void red_add(double* p, float v) { atomicAdd(p, widen(v)); }
+// ------------------------------------------------------- FP64 accumulation --
+// FP32 terms are converted exactly to FP64 and added with one red each: the
+// only FP64 steps.  (The conversion uses the FP64 conversion unit; at well
+// under one conversion per voxel crossing it is far from that unit's rate.)
+__device__ __forceinline__ void red_add(double* p, float v) { atomicAdd(p, (double)v); }
 
 // ------------------------------------------------------ phase functions --
 // Henyey-Greenstein (cloud) and Rayleigh (air), normalised on the sphere.

@@ -16,9 +16,26 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
     v = (v | (v << 2)) & 0x09249249u;
     return v;
 }
-__device__ __forceinline__ uint32_t event_bin(uint32_t pv, int bits, int shift) {
-    const uint32_t m = (1u << bits) - 1u;
-    const uint32_t bx = (pv & 511u) >> shift, by = ((pv >> 9) & 511u) >> shift, bz = ((pv >> 18) & 511u) >> shift;
+// sub-voxel cell (0 .. 2^sub - 1) of coordinate c in voxel i along one axis
+__device__ __forceinline__ uint32_t sub_cell(float c, float o, float inv_vox, uint32_t i, int sub) {
+    const int q = (int)floorf((c - o) * inv_vox * (float)(1 << sub)) - (int)(i << sub);
+    return (uint32_t)min(max(q, 0), (1 << sub) - 1);
+}
+// Bin of an event: Morton code of its voxel coordinates (>> shift), with
+// `sub` bits of its position inside the voxel appended per axis, so that
+// events of one voxel are ordered by where they lie in it.  Only the order
+// of events depends on the bin; their voxel is the record's.
+__device__ __forceinline__ uint32_t event_bin(const DevScene& S, const Events& E, uint4 a) {
+    const uint32_t pv = a.w & kVoxMask;
+    const uint32_t m = (1u << E.bin_bits) - 1u;
+    const uint32_t ix = pv & 511u, iy = (pv >> 9) & 511u, iz = (pv >> 18) & 511u;
+    uint32_t bx = ix >> E.bin_shift, by = iy >> E.bin_shift, bz = iz >> E.bin_shift;
+    if (E.bin_sub) {
+        const int s = E.bin_sub;
+        bx = (bx << s) | sub_cell(__uint_as_float(a.x), S.ox, S.inv_vox, ix, s);
+        by = (by << s) | sub_cell(__uint_as_float(a.y), S.oy, S.inv_vox, iy, s);
+        bz = (bz << s) | sub_cell(__uint_as_float(a.z), S.oz, S.inv_vox, iz, s);
+    }
     return spread3(bx & m) | (spread3(by & m) << 1) | (spread3(bz & m) << 2);
 }
 

@@ -24,7 +24,8 @@ namespace pt {
 namespace {
 
 
-__global__ void __launch_bounds__(128) k_ev_hist(SortedPaths P, Events E, int max_orders) {
+__global__ void __launch_bounds__(128) k_ev_hist(DevScene S, SortedPaths P, Events E) {
+    const int max_orders = S.max_orders;
     __shared__ SharedBk sb;
     for (int k = threadIdx.x; k <= kBuckets; k += blockDim.x) {
         sb.po[k] = P.buckets->path_off[k];
@@ -35,13 +36,12 @@ __global__ void __launch_bounds__(128) k_ev_hist(SortedPaths P, Events E, int ma
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     PathRef pr;
     if (!locate(sb.po, sb.ro, sb.cnt, max_orders, j, pr)) return;
-    for (int e = 1; e <= pr.B; ++e) {
-        const uint32_t pv = P.rec_a[pr.base + (uint64_t)e * pr.stride].w & kVoxMask;
-        atomicAdd(E.hist + event_bin(pv, E.bin_bits, E.bin_shift), 1u);
-    }
+    for (int e = 1; e <= pr.B; ++e)
+        atomicAdd(E.hist + event_bin(S, E, P.rec_a[pr.base + (uint64_t)e * pr.stride]), 1u);
 }
 
-__global__ void __launch_bounds__(128) k_ev_scatter(SortedPaths P, Events E, int max_orders) {
+__global__ void __launch_bounds__(128) k_ev_scatter(DevScene S, SortedPaths P, Events E) {
+    const int max_orders = S.max_orders;
     __shared__ SharedBk sb;
     for (int k = threadIdx.x; k <= kBuckets; k += blockDim.x) {
         sb.po[k] = P.buckets->path_off[k];
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(128) k_ev_scatter(SortedPaths P, Events E, int
         const uint64_t rec = pr.base + (uint64_t)e * pr.stride;
         const uint4 a = P.rec_a[rec];
         const float4 b = P.rec_b[rec];
-        const uint32_t pos = atomicAdd(E.cursor + event_bin(a.w & kVoxMask, E.bin_bits, E.bin_shift), 1u);
+        const uint32_t pos = atomicAdd(E.cursor + event_bin(S, E, a), 1u);
         E.a[pos] = make_uint4(a.x, a.y, a.z, a.w & kVoxMask);
         E.b[pos] = make_float4(b.x, b.y, b.z, 0.0f);
         E.of_rec[rec] = pos;
@@ -149,12 +149,12 @@ void launch_events(const DevScene& S, const SortedPaths& P, const Events& E, cud
     const unsigned g = blocks(P.n_max, 128);
     if (g == 0) return;
     cudaMemsetAsync(E.hist, 0, sizeof(uint32_t) * E.n_bins, st);
-    k_ev_hist<<<g, 128, 0, st>>>(P, E, S.max_orders);
+    k_ev_hist<<<g, 128, 0, st>>>(S, P, E);
     const uint32_t nb = (E.n_bins + kScanItems - 1) / kScanItems;   // <= 4096 for 2^24 bins
     k_scan_blocks<<<nb, 1024, 0, st>>>(E.hist, E.cursor, E.partial, E.n_bins);
     k_scan_blocks<<<1, 1024, 0, st>>>(E.partial, E.partial + kScanItems, E.partial + 2 * kScanItems, nb);
     k_scan_add<<<nb, 1024, 0, st>>>(E.cursor, E.partial + kScanItems, E.n_bins);
-    k_ev_scatter<<<g, 128, 0, st>>>(P, E, S.max_orders);
+    k_ev_scatter<<<g, 128, 0, st>>>(S, P, E);
 }
 
 void launch_reweight(const DevScene& S, const SortedPaths& P, const Events& E, const float* beta_t,

@@ -40,6 +40,7 @@ struct Events {
     uint32_t n_bins;
     int bin_bits;      // Morton bits per axis (<= 8: at most 2^24 bins)
     int bin_shift;     // voxel coordinates >> bin_shift give the bin coordinates
+    int bin_sub;       // sub-voxel bits per axis appended to the voxel coordinates
     uint64_t cap;      // event capacity
 };
 
