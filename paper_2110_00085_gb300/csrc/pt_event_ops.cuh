@@ -184,6 +184,52 @@ __device__ __forceinline__ void red_runs(double* __restrict__ grad, int idx, flo
     if (tail && idx >= 0 && s != 0.0f) red_add(grad + idx, s);
 }
 
+// 8-bit value with its bits moved to the even positions
+__device__ __forceinline__ uint32_t spread2(uint32_t v) {
+    v &= 0xffu;
+    v = (v | (v << 4)) & 0x0f0fu;
+    v = (v | (v << 2)) & 0x3333u;
+    v = (v | (v << 1)) & 0x5555u;
+    return v;
+}
+
+// Lane that should march the ray of this step's lane order: the warp's rays
+// to one camera are ordered by a 2D Morton code of where their events lie
+// across the direction to the camera (relative to the first live lane's
+// event, in 1/32 voxel, +-4 voxels), so that lanes whose rays run side by
+// side are adjacent and the run merge of red_runs finds their shared
+// voxels.  Lanes without a ray go last.  A bitonic sort of the 32 keys
+// (lane number in the low bits: all keys distinct) gives the permutation.
+__device__ __forceinline__ int lateral_order(const DevScene& S, float3 x, float3 dir, bool live, int lane) {
+    const unsigned full = 0xffffffffu;
+    const int ld = __ffs(__ballot_sync(full, live)) - 1;
+    const float3 d0 = make_float3(__shfl_sync(full, dir.x, ld), __shfl_sync(full, dir.y, ld),
+                                  __shfl_sync(full, dir.z, ld));
+    const float3 rel = make_float3(x.x - __shfl_sync(full, x.x, ld), x.y - __shfl_sync(full, x.y, ld),
+                                   x.z - __shfl_sync(full, x.z, ld));
+    // an orthonormal pair across d0 (Duff et al., JCGT 2017)
+    const float sg = copysignf(1.0f, d0.z);
+    const float ia = -1.0f / (sg + d0.z);
+    const float bb = d0.x * d0.y * ia;
+    const float3 e1 = make_float3(1.0f + sg * d0.x * d0.x * ia, sg * bb, -sg * d0.x);
+    const float3 e2 = make_float3(bb, sg + d0.y * d0.y * ia, -d0.y);
+    const float k = 32.0f * S.inv_vox;
+    const int qu = min(max((int)floorf(dot3(rel, e1) * k) + 128, 0), 255);
+    const int qv = min(max((int)floorf(dot3(rel, e2) * k) + 128, 0), 255);
+    uint32_t key = live ? (((spread2((uint32_t)qu) | (spread2((uint32_t)qv) << 1)) << 5) | (uint32_t)lane)
+                        : ((1u << 21) | (uint32_t)lane);
+#pragma unroll
+    for (int k2 = 2; k2 <= 32; k2 <<= 1) {
+#pragma unroll
+        for (int j = k2 >> 1; j > 0; j >>= 1) {
+            const uint32_t o = __shfl_xor_sync(full, key, j);
+            const bool keep_min = ((lane & j) == 0) == ((lane & k2) == 0);
+            key = keep_min ? min(key, o) : max(key, o);
+        }
+    }
+    return (int)(key & 31u);
+}
+
 // Warp-synchronous: every lane of the warp calls it (lanes past the last
 // event pass pos >= n_events).
 __device__ __forceinline__ void event_grad_warp(const DevScene& S, const DevCam* cams, const Events& E,
@@ -229,15 +275,25 @@ __device__ __forceinline__ void event_grad_warp(const DevScene& S, const DevCam*
         }
         bool live = a != 0.0f;
         if (!__any_sync(full, live)) continue;
+        // march the rays in this camera's lateral order (A and the vertex
+        // terms above stay with the event's own lane)
+        const int src = lateral_order(S, x, dir, live, lane);
+        const float3 xs = make_float3(__shfl_sync(full, x.x, src), __shfl_sync(full, x.y, src),
+                                      __shfl_sync(full, x.z, src));
+        const float3 ds = make_float3(__shfl_sync(full, dir.x, src), __shfl_sync(full, dir.y, src),
+                                      __shfl_sync(full, dir.z, src));
+        const uint32_t pvs = __shfl_sync(full, pv, src);
+        const float as = __shfl_sync(full, a, src);
+        live = __shfl_sync(full, (int)live, src) != 0;
         Dda r;
-        r.init(S, x, dir, pv, __int_as_float(0x7f800000));
+        r.init(S, xs, ds, pvs, __int_as_float(0x7f800000));
         while (__any_sync(full, live)) {
             int idx = -1 - lane;   // never equal across lanes
             float val = 0.0f;
             if (live) {
                 const float tn = r.next();
                 idx = r.idx;
-                val = -a * r.seg(tn);
+                val = -as * r.seg(tn);
                 live = r.step(S, tn);
             }
             red_runs(grad, idx, val, lane);
