@@ -158,11 +158,12 @@ __device__ __forceinline__ void event_forward_one(const DevScene& S, const DevCa
 // gradient, per event: shadow-ray scatters -a l, local-estimate vertex
 // terms a h(x_b, mu_bd), and A_e = sum_d a for the per-path suffix sums.
 // The warp takes the cameras one at a time and walks its 32 shadow rays in
-// step.  Lanes holding events of one voxel are adjacent and their rays stay
-// together, so at each step the -a l terms of adjacent lanes in the same
-// voxel are summed (a segmented shuffle scan over runs of equal voxel ids,
-// 8 lanes deep) and one FP64 red per run (per 8 lanes of a longer run)
-// leaves the warp.
+// step, ordered across the direction to the camera (lateral_order), so that
+// lanes whose rays run side by side are adjacent.  At each step the -a l
+// terms of adjacent lanes in the same voxel are summed (a segmented shuffle
+// scan over runs of equal voxel ids, kRunChunk lanes deep) and one FP64 red
+// per run (per kRunChunk lanes of a longer run) leaves the warp.
+constexpr int kRunChunk = 8;    // lanes summed per red at most (a power of two; 16 measured no faster)
 __device__ __forceinline__ void red_runs(double* __restrict__ grad, int idx, float val, int lane) {
     const unsigned full = 0xffffffffu;
     const int prev = __shfl_up_sync(full, idx, 1);
@@ -172,15 +173,15 @@ __device__ __forceinline__ void red_runs(double* __restrict__ grad, int idx, flo
         return;
     }
     const int start = 31 - __clz(heads & ((2u << lane) - 1u));   // first lane of my run
-    const int chunk = start + ((lane - start) & ~7);               // first lane of my 8-lane chunk
+    const int chunk = start + ((lane - start) & ~(kRunChunk - 1));  // first lane of my chunk
     float s = val;
 #pragma unroll
-    for (int d = 1; d < 8; d <<= 1) {
+    for (int d = 1; d < kRunChunk; d <<= 1) {
         const float o = __shfl_up_sync(full, s, d);
         if (lane - d >= chunk) s += o;
     }
     // the last lane of a run or of a chunk holds the chunk's sum
-    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u) || ((lane - start) & 7) == 7;
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u) || ((lane - start) & (kRunChunk - 1)) == kRunChunk - 1;
     if (tail && idx >= 0 && s != 0.0f) red_add(grad + idx, s);
 }
 
