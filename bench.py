@@ -268,6 +268,29 @@ def run_batch(args, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def profiled_traffic(call, n):
+    """DRAM bytes per call of ``call`` from the committed ncu record, scaled
+    to n paths; None unless the kernel sources still hash to the profiled
+    ones (a changed kernel has no counters yet)."""
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, "profiles", f"traffic_{call}_noise128.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#") and "=" in line:
+            k, v = line.split("=", 1)
+            rec[k.strip()] = v.strip()
+    h = hashlib.sha1()
+    for f in ("pt_event_ops.cuh", "pt_events.cu", "pt_device.cuh", "pt_kernels.cuh"):
+        h.update(open(os.path.join(here, "paper_2110_00085_gb300", "csrc", f), "rb").read())
+    if rec.get("call") != call or rec.get("source_sha1_16") != h.hexdigest()[:16]:
+        return None
+    return float(rec["bytes_per_call"]) * n / float(rec["paths"])
+
+
 def calibrate_matched(args, ws, scene, gt_img, beta0, n, lr, seed, reuse_ms):
     """Resample budget of equal gradient error and its step time.
 
@@ -446,8 +469,12 @@ def run_native(args, ws, rank, local):
     achieved = alu_per_cross * crosses / (avg[dom] * 1e-3) / 1e12      # T ALU lane-ops/s
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     peak = 152 * 64 * sm_mhz * 1e6 / 1e12   # 152 SMs x 4 partitions x 16 ALU lanes per clock
+    traffic = profiled_traffic(dom, n)
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernels at 2^20 "
+                               "paths (profiles/traffic_render_grad_noise128.txt), scaled by paths")
+                              if traffic is not None else None,
             "peak_source": f"derived: 152 SMs x 64 ALU-pipe lanes/clock x {sm_mhz:.0f} MHz ({pk_src} max SM clock)",
             "work": f"{alu_per_cross:.0f} ALU ops per voxel crossing x {crosses:.3e} crossings per call",
             "per_call_ms": {k: round(v, 3) for k, v in avg.items()},
