@@ -1,0 +1,151 @@
+"""Parity at the full size of the timed workload (noise128: 128^3 grid, 15
+cameras of 128x128, 2^24 paths), in the launch configuration the bench
+times: one paths_store of all 2^24 paths, paths_reweight with the
+contribution cache and render_grad from the cache.
+
+No oracle run covers 2^24 paths, so the full launch is checked on outputs
+the oracle computes path by path and on properties that hold at any size:
+- fingerprints of sampled path ids (up to the last one) equal the oracle's;
+- single-path stores of sampled ids, with the full run's normalisation,
+  give the oracle's images and gradient element by element;
+- the full launch equals the sum of two half launches (images to FP64
+  summation order, gradient to the FP32 pre-sums of the merged reds);
+- reweighting at beta_ref reproduces the store's own images, the tallies
+  balance energy, and the path buckets and events match the tallies.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2110_00085_gb300 import native as N
+from paper_2110_00085_gb300 import synth
+
+from _parity import assert_grad_close, assert_images_close, t32, t64
+
+pytestmark = pytest.mark.gpu
+
+FULL = 1 << 24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    torch.cuda.set_device(0)
+
+
+@pytest.fixture(scope="module")
+def case():
+    sc = synth.config(3, n_paths=FULL)
+    rng = np.random.default_rng(24)
+    br = sc.beta_cloud.astype(np.float32)
+    bt = (sc.beta_cloud * rng.uniform(0.9, 1.15, size=sc.beta_cloud.shape)).astype(np.float32)
+    scene = N.Scene(sc)
+    dl = rng.standard_normal(scene.n_pixels)
+    return sc, scene, br, bt, dl
+
+
+@pytest.fixture(scope="module")
+def full_run(case):
+    sc, scene, br, bt, dl = case
+    fp = torch.zeros(FULL, dtype=torch.int64, device="cuda")
+    tal = torch.zeros(N.TALLY_COUNT, dtype=torch.float64, device="cuda")
+    ref = scene.new_images()
+    p = N.Paths(scene).store(t32(br), FULL, sc.seed, images_ref=ref, tallies=tal, fingerprints=fp)
+    same = p.reweight(t32(br), cache=False)
+    img = p.reweight(t32(bt), cache=True)
+    g = p.grad(t32(bt), t64(dl), cache=True)
+    torch.cuda.synchronize()
+    scene.check()
+    out = {"fp": fp.cpu().numpy().view(np.uint64), "tallies": dict(zip(N.TALLY_NAMES, tal.cpu().numpy())),
+           "ref": ref.cpu().numpy(), "same": same.cpu().numpy(), "img": img.cpu().numpy(),
+           "grad": g.cpu().numpy(), "info": p.info()}
+    p.close()
+    return out
+
+
+def test_fullsize_fingerprints_match_oracle_on_sampled_paths(case, full_run):
+    sc, scene, br, bt, dl = case
+    rng = np.random.default_rng(5)
+    ids = np.unique(np.concatenate([rng.integers(0, FULL, 254), [0, FULL - 1]]))
+    bad = 0
+    for pid in ids:
+        o = O.render(sc, br, first=int(pid), n=1, n_norm=FULL, fingerprints=True)["fingerprints"][0]
+        bad += int(o != full_run["fp"][pid])
+    assert bad <= 2, f"{bad} of {len(ids)} sampled paths take other discrete decisions"
+
+
+def test_fullsize_sampled_paths_match_oracle_elementwise(case, full_run):
+    """Path ids from the whole range, each stored alone with the full run's
+    normalisation, summed on both sides and compared element by element."""
+    sc, scene, br, bt, dl = case
+    rng = np.random.default_rng(6)
+    ids = [int(i) for i in rng.integers(0, FULL, 24)] + [FULL - 1]
+    gi = scene.new_images()
+    gg = torch.zeros(scene.n_voxels, dtype=torch.float64, device="cuda")
+    oi = np.zeros(scene.n_pixels)
+    og = np.zeros(scene.n_voxels)
+    oabs = np.zeros(scene.n_voxels)
+    ocond = np.zeros(scene.n_voxels)
+    icond = np.zeros(scene.n_pixels)
+    used = 0
+    for pid in ids:
+        o = O.render(sc, br, bt, first=pid, n=1, n_norm=FULL, dldi=dl, grad_abs=True, grad_cond=True,
+                     image_cond=True, fingerprints=True)
+        if o["fingerprints"][0] != full_run["fp"][pid]:
+            continue    # a near-tie of a discrete decision: compared by neither side
+        one = N.Paths(scene).store(t32(br), 1, sc.seed, first=pid, n_norm=FULL)
+        one.reweight(t32(bt), gi, cache=True, accumulate=True)
+        one.grad(t32(bt), t64(dl), gg, cache=True, accumulate=True)
+        one.close()
+        oi += o["images"]; og += o["grad"]; oabs += o["grad_abs"]; ocond += o["grad_cond"]
+        icond += o["image_cond"]
+        used += 1
+    torch.cuda.synchronize()
+    assert used >= len(ids) - 2
+    assert np.abs(oi).max() > 0 and np.abs(og).max() > 0
+    assert_images_close(gi.cpu().numpy(), oi, cond=icond, what="sampled paths, images")
+    assert_grad_close(gg.cpu().numpy(), og, oabs, ocond, what="sampled paths, gradient")
+
+
+def test_fullsize_launch_equals_two_half_launches(case, full_run):
+    sc, scene, br, bt, dl = case
+    half = FULL // 2
+    img = scene.new_images()
+    g = torch.zeros(scene.n_voxels, dtype=torch.float64, device="cuda")
+    for first in (0, half):
+        p = N.Paths(scene).store(t32(br), half, sc.seed, first=first, n_norm=FULL)
+        p.reweight(t32(bt), img, cache=True, accumulate=True)
+        p.grad(t32(bt), t64(dl), g, cache=True, accumulate=True)
+        torch.cuda.synchronize()
+        p.close()
+    scene.check()
+    full_img, full_g = full_run["img"], full_run["grad"]
+    assert np.abs(full_img).max() > 0
+    assert_images_close(img.cpu().numpy(), full_img, rtol=1e-9, what="half + half vs full, images")
+    g = g.cpu().numpy()
+    scale = np.abs(full_g).max()
+    # the merged reds pre-sum up to 8 FP32 terms, grouped differently in the
+    # three launches: relative 1e-6 of the field, and 1e-5 per voxel on all
+    # but a few voxels where the terms cancel
+    assert np.linalg.norm(g - full_g) <= 1e-6 * np.linalg.norm(full_g)
+    off = np.abs(g - full_g) > 1e-5 * np.abs(full_g) + 1e-9 * scale
+    assert off.mean() < 1e-3, f"{off.sum()} voxels off"
+
+
+def test_fullsize_invariants(full_run):
+    # r == 1 at beta_ref: the store's own images, up to FP64 summation order
+    assert np.abs(full_run["ref"]).max() > 0
+    assert np.allclose(full_run["same"], full_run["ref"], rtol=1e-11, atol=0)
+    T = full_run["tallies"]
+    lhs = T["injected"] + T["rr_gain"]
+    rhs = T["escaped"] + T["absorbed"] + T["truncated"] + T["rr_killed"]
+    assert abs(lhs - rhs) < 1e-5 * lhs
+    info = full_run["info"]
+    bk = info["bucket"]
+    assert sum(bk) == int(T["entered"])
+    assert sum(k * c for k, c in enumerate(bk)) == int(T["collisions"])
+    assert info["n_records"] == sum((k + 1) * c for k, c in enumerate(bk) if k >= 1)
