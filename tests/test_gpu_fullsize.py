@@ -12,6 +12,9 @@ the oracle computes path by path and on properties that hold at any size:
   summation order, gradient to the FP32 pre-sums of the merged reds);
 - reweighting at beta_ref reproduces the store's own images, the tallies
   balance energy, and the path buckets and events match the tallies.
+The batched workload (16 uneven scenes) is checked at its full size too:
+every launch shape against the per-scene calls, and sampled fingerprints of
+every scene against the oracle.
 """
 import numpy as np
 import pytest
@@ -149,3 +152,49 @@ def test_fullsize_invariants(full_run):
     assert sum(bk) == int(T["entered"])
     assert sum(k * c for k, c in enumerate(bk)) == int(T["collisions"])
     assert info["n_records"] == sum((k + 1) * c for k, c in enumerate(bk) if k >= 1)
+
+
+def test_batch_fullsize_matches_per_scene_calls_and_oracle_fingerprints():
+    """The batched workload at its full size (16 scenes of grid sides 32-128,
+    5-21 cameras of 64x64, 2^20-2^23 paths each): the batched launches under
+    the default and the grouped register-capped shapes agree with the
+    per-scene calls on every scene, and sampled paths of every scene take
+    the oracle's discrete decisions (scene id in the Philox counter)."""
+    specs = synth.batch_config(5)
+    rng = np.random.default_rng(44)
+    scenes = [N.Scene(sc, scene_id=i) for i, sc in enumerate(specs)]
+    br = [sc.beta_cloud.astype(np.float32) for sc in specs]
+    bt = [(sc.beta_cloud * rng.uniform(0.9, 1.15, size=sc.beta_cloud.shape)).astype(np.float32) for sc in specs]
+    dl = [rng.standard_normal(s.n_pixels) for s in scenes]
+    fps, paths, ref_img, ref_g = [], [], [], []
+    for s, sc, b, bb, d in zip(scenes, specs, br, bt, dl):
+        fp = torch.zeros(sc.n_paths, dtype=torch.int64, device="cuda")
+        p = N.Paths(s).store(t32(b), sc.n_paths, sc.seed, fingerprints=fp)
+        ref_img.append(p.reweight(t32(bb), cache=True).cpu().numpy())
+        ref_g.append(p.grad(t32(bb), t64(d), cache=True).cpu().numpy())
+        fps.append(fp.cpu().numpy().view(np.uint64))
+        paths.append(p)
+    imgs = [s.new_images() for s in scenes]
+    grads = [torch.zeros(s.n_voxels, dtype=torch.float64, device="cuda") for s in scenes]
+    batch = N.Batch(paths)
+    batch.bind([t32(b) for b in bt], imgs, [t64(d) for d in dl], grads)
+    for shape in (batch.shape, (1, 0)):
+        batch.set_launch(*shape)
+        batch.reweight(cache=True)
+        batch.grad(cache=True)
+        torch.cuda.synchronize()
+        for k, s in enumerate(scenes):
+            s.check()
+            assert np.abs(ref_img[k]).max() > 0
+            assert_images_close(imgs[k].cpu().numpy(), ref_img[k], rtol=1e-6, what=f"shape {shape} scene {k}")
+            g = grads[k].cpu().numpy()
+            assert np.linalg.norm(g - ref_g[k]) <= 1e-6 * np.linalg.norm(ref_g[k])
+    batch.close()
+    for p in paths:
+        p.close()
+    bad = 0
+    for k, sc in enumerate(specs):
+        for pid in rng.integers(0, sc.n_paths, 4):
+            o = O.render(sc, br[k], first=int(pid), n=1, n_norm=sc.n_paths, fingerprints=True, scene_id=k)
+            bad += int(o["fingerprints"][0] != fps[k][pid])
+    assert bad <= 1
