@@ -144,9 +144,16 @@ int render_forward(const pt_scene* scene, const float* beta_cloud,
  * (stable in path id), as compact vertex records.  The handle keeps a copy
  * of beta_cloud as M_ref.  *paths == NULL creates a handle (owned by the
  * caller, freed with paths_free); an existing handle of the same scene is
- * reused, growing its buffers if n_paths exceeds its capacity.  images_ref
- * (nullable) receives the plain estimate under M_ref (as render_forward).
- * Allocation (first use or growth) synchronises the device.
+ * reused.  images_ref (nullable) receives the plain estimate under M_ref (as
+ * render_forward).
+ * Memory: the sampled records (every path's maximum number of slots) live
+ * only until the sort, in a stream-ordered pool of this library that keeps
+ * its memory for later stores; the kept records, events and the
+ * contribution cache are sized from the actual record and event counts
+ * (1/8 headroom), which paths_store reads after its counting sort: the call
+ * synchronises the stream once, and growing a buffer synchronises again.
+ * n_paths < 2^32 per handle; larger path sets are stored as several handles
+ * over ranges of path ids (first_path) sharing n_norm.
  */
 int paths_store(const pt_scene* scene, const float* beta_cloud,
                 uint64_t first_path, uint64_t n_paths, double n_norm,

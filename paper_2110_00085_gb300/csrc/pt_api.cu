@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -148,21 +149,17 @@ struct pt_scene {
 
 struct pt_paths {
     const pt_scene* scene = nullptr;
-    uint64_t cap = 0;          // paths per store
     uint64_t n = 0;            // paths of the latest store
+    uint64_t rec_cap = 0;      // sorted records (and record-to-event map entries) the buffers hold
     int slots = 0;             // max_orders + 1
     float inv_norm = 1.0f;
     int64_t V = 0;
     float* beta_ref = nullptr;
     float* dbeta = nullptr;
-    uint4* ua = nullptr;
-    float4* ub = nullptr;
-    uint8_t* cnt = nullptr;
-    uint4* sa = nullptr;
-    float4* sb = nullptr;
-    uint32_t* blk = nullptr;
+    uint4* sa = nullptr;       // sorted records (stream A)
+    float4* sb = nullptr;      // sorted records (stream B)
     Buckets* bk = nullptr;
-    Events ev{};
+    Events ev{};               // ev.cap = events the buffers hold
     float* cache = nullptr;
     uint64_t cache_cap = 0;    // floats
     uint64_t bytes = 0;
@@ -170,13 +167,40 @@ struct pt_paths {
 };
 
 namespace {
+// Stream-ordered pool of this library for the transient buffers of
+// paths_store (one per device, created on first use).  It keeps the memory
+// it has mapped (release threshold: unlimited), so repeated stores reuse it
+// instead of mapping gigabytes again; no other allocator is affected.
+cudaMemPool_t store_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = pool;
+    }
+    return pools[dev];
+}
+
 void free_paths_buffers(pt_paths* p) {
-    cudaFree(p->beta_ref); cudaFree(p->dbeta); cudaFree(p->ua); cudaFree(p->ub); cudaFree(p->cnt);
-    cudaFree(p->sa); cudaFree(p->sb); cudaFree(p->blk); cudaFree(p->bk); cudaFree(p->cache);
+    cudaFree(p->beta_ref); cudaFree(p->dbeta); cudaFree(p->sa); cudaFree(p->sb); cudaFree(p->bk); cudaFree(p->cache);
     cudaFree(p->ev.a); cudaFree(p->ev.b); cudaFree(p->ev.of_rec); cudaFree(p->ev.val); cudaFree(p->ev.hist);
     cudaFree(p->ev.cursor); cudaFree(p->ev.partial);
-    p->beta_ref = p->dbeta = nullptr; p->ua = p->sa = nullptr; p->ub = p->sb = nullptr; p->cnt = nullptr;
-    p->blk = nullptr; p->bk = nullptr; p->cache = nullptr; p->cache_cap = 0; p->cap = 0; p->bytes = 0;
+    p->beta_ref = p->dbeta = nullptr; p->sa = nullptr; p->sb = nullptr;
+    p->bk = nullptr; p->cache = nullptr; p->cache_cap = 0; p->rec_cap = 0; p->bytes = 0;
     p->ev = Events{};
 }
 
@@ -400,26 +424,13 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
     }
     p->scene = sc;
     const int slots = sc->ds.max_orders + 1;
-    if (p->cap < n || p->slots != slots) {
+    int rc;
+    if (!p->beta_ref || p->V != sc->ds.V || p->slots != slots) {
+        // buffers of fixed size: grids, bucket table, event bins
         if (!created) PT_CUDA(cudaStreamSynchronize(st));
         free_paths_buffers(p);
-        const uint64_t nblk = (n + 255) / 256;
-        int rc;
         uint64_t by = 0;
         p->V = sc->ds.V;
-        if ((rc = dev_alloc(&p->beta_ref, (uint64_t)p->V, &by, "beta_ref")) ||
-            (rc = dev_alloc(&p->dbeta, (uint64_t)p->V, &by, "dbeta")) ||
-            (rc = dev_alloc(&p->ua, n * slots, &by, "records A")) ||
-            (rc = dev_alloc(&p->ub, n * slots, &by, "records B")) ||
-            (rc = dev_alloc(&p->cnt, n, &by, "counts")) ||
-            (rc = dev_alloc(&p->sa, n * slots, &by, "sorted A")) ||
-            (rc = dev_alloc(&p->sb, n * slots, &by, "sorted B")) ||
-            (rc = dev_alloc(&p->blk, nblk * kBuckets, &by, "block histogram")) ||
-            (rc = dev_alloc(&p->bk, 1, &by, "buckets"))) {
-            free_paths_buffers(p);
-            if (created) delete p;
-            return rc;
-        }
         Events& E = p->ev;
         E.bin_bits = event_bin_bits(sc->ds);
         E.bin_shift = 0;
@@ -432,10 +443,9 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
         E.bin_sub = std::min(2, 8 - E.bin_bits);
         E.bin_bits += E.bin_sub;
         E.n_bins = 1u << (3 * E.bin_bits);
-        E.cap = n * (uint64_t)sc->ds.max_orders;
-        if ((rc = dev_alloc(&E.a, E.cap, &by, "events A")) || (rc = dev_alloc(&E.b, E.cap, &by, "events B")) ||
-            (rc = dev_alloc(&E.val, E.cap, &by, "event values")) ||
-            (rc = dev_alloc(&E.of_rec, n * slots, &by, "record-to-event map")) ||
+        if ((rc = dev_alloc(&p->beta_ref, (uint64_t)p->V, &by, "beta_ref")) ||
+            (rc = dev_alloc(&p->dbeta, (uint64_t)p->V, &by, "dbeta")) ||
+            (rc = dev_alloc(&p->bk, 1, &by, "buckets")) ||
             (rc = dev_alloc(&E.hist, E.n_bins, &by, "event bins")) ||
             (rc = dev_alloc(&E.cursor, E.n_bins, &by, "event bin cursors")) ||
             (rc = dev_alloc(&E.partial, 3 * 4096, &by, "scan partials"))) {
@@ -443,25 +453,93 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
             if (created) delete p;
             return rc;
         }
-        p->cap = n;
         p->slots = slots;
         p->bytes = by;
     }
     p->n = n;
     p->inv_norm = (float)(1.0 / n_norm);
     p->cache_valid = false;
+    *pp = p;
+
+    // The sampled records (slot-major, every path's maximum slots) live only
+    // until the sort: stream-ordered allocations, returned to the pool after
+    // the scatter.  The kept arrays are sized from the actual record and
+    // event counts, read once the counting sort has run.
+    StoreBuf sbuf{nullptr, nullptr, nullptr, n};
+    uint32_t* blk = nullptr;
+    const uint64_t nblk = sort_blocks(n);
+    cudaMemPool_t pool = store_pool();
+    auto tmp = [&](void** q, uint64_t bytes, const char* what) -> int {
+        const cudaError_t e = pool ? cudaMallocFromPoolAsync(q, bytes ? bytes : 16, pool, st)
+                                   : cudaMallocAsync(q, bytes ? bytes : 16, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PT_E_OOM, "paths_store: no device memory for %s (%llu bytes)", what,
+                        (unsigned long long)bytes);
+        }
+        return PT_OK;
+    };
+    auto release = [&]() {
+        for (void* q : {(void*)sbuf.rec_a, (void*)sbuf.rec_b, (void*)sbuf.cnt, (void*)blk})
+            if (q) cudaFreeAsync(q, st);
+    };
+    if ((rc = tmp((void**)&sbuf.rec_a, sizeof(uint4) * n * slots, "sampled records A")) ||
+        (rc = tmp((void**)&sbuf.rec_b, sizeof(float4) * n * slots, "sampled records B")) ||
+        (rc = tmp((void**)&sbuf.cnt, sizeof(uint8_t) * n, "collision counts")) ||
+        (rc = tmp((void**)&blk, sizeof(uint32_t) * nblk * kBuckets, "block histogram"))) {
+        release();
+        return rc;
+    }
     PT_CUDA(cudaMemcpyAsync(p->beta_ref, beta, sizeof(float) * p->V, cudaMemcpyDeviceToDevice, st));
     if (images_ref && !(flags & PT_ACCUMULATE)) PT_CUDA(cudaMemsetAsync(images_ref, 0, sizeof(double) * sc->n_pixels, st));
-    StoreBuf sbuf{p->ua, p->ub, p->cnt, n};
     // without images_ref the kernel traces flights only (no shadow rays)
     launch_sample(sc->ds, beta, first, n, p->inv_norm, seed, epoch, images_ref, tallies, fps, &sbuf, st);
-    if (int rc = launch_status("paths_store")) return rc;
-    launch_sort(sbuf, n, slots, p->blk, p->bk, sc->ds.n_cams, p->sa, p->sb, st);
-    if (int rc = launch_status("paths_store sort")) return rc;
+    if ((rc = launch_status("paths_store"))) { release(); return rc; }
+    launch_sort_count(sbuf, n, slots, blk, p->bk, st);
+    if ((rc = launch_status("paths_store sort"))) { release(); return rc; }
+    Buckets hb;
+    if (cudaMemcpyAsync(&hb, p->bk, sizeof(Buckets), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        release();
+        return launch_status("paths_store counts");
+    }
+    const uint64_t n_rec = hb.rec_off[kBuckets], n_ev = hb.n_events;
+    // grow the kept arrays (1/8 headroom, so that later stores of a similar
+    // path set reuse them); a grown handle must be bound again in a batch
+    auto grow = [](uint64_t need) { return need + need / 8 + 1024; };
+    if (p->rec_cap < n_rec || !p->sa) {
+        cudaFree(p->sa); cudaFree(p->sb); cudaFree(p->ev.of_rec);
+        p->sa = nullptr; p->sb = nullptr; p->ev.of_rec = nullptr;
+        p->bytes -= p->rec_cap * (sizeof(uint4) + sizeof(float4) + sizeof(uint32_t));
+        p->rec_cap = 0;
+        const uint64_t c = grow(n_rec);
+        if ((rc = dev_alloc(&p->sa, c, &p->bytes, "sorted records A")) ||
+            (rc = dev_alloc(&p->sb, c, &p->bytes, "sorted records B")) ||
+            (rc = dev_alloc(&p->ev.of_rec, c, &p->bytes, "record-to-event map"))) {
+            release();
+            return rc;
+        }
+        p->rec_cap = c;
+    }
+    if (p->ev.cap < n_ev || !p->ev.a) {
+        Events& E = p->ev;
+        cudaFree(E.a); cudaFree(E.b); cudaFree(E.val);
+        E.a = nullptr; E.b = nullptr; E.val = nullptr;
+        p->bytes -= E.cap * (sizeof(uint4) + sizeof(float4) + sizeof(float));
+        E.cap = 0;
+        const uint64_t c = grow(n_ev);
+        if ((rc = dev_alloc(&E.a, c, &p->bytes, "events A")) || (rc = dev_alloc(&E.b, c, &p->bytes, "events B")) ||
+            (rc = dev_alloc(&E.val, c, &p->bytes, "event values"))) {
+            release();
+            return rc;
+        }
+        E.cap = c;
+    }
+    launch_sort_scatter(sbuf, n, blk, p->bk, p->sa, p->sb, st);
+    release();
+    if ((rc = launch_status("paths_store sort"))) return rc;
     launch_events(sc->ds, sorted_view(p), p->ev, st);
-    if (int rc = launch_status("paths_store events")) return rc;
-    *pp = p;
-    return PT_OK;
+    return launch_status("paths_store events");
 }
 
 int paths_reweight(pt_paths* p, const float* beta_t, double* images, uint32_t flags, void* stream) {
@@ -486,7 +564,7 @@ int paths_reweight(pt_paths* p, const float* beta_t, double* images, uint32_t fl
     if (!(flags & PT_ACCUMULATE)) PT_CUDA(cudaMemsetAsync(images, 0, sizeof(double) * sc->n_pixels, st));
     launch_delta(beta_t, p->beta_ref, p->dbeta, p->V, st);
     launch_reweight(sc->ds, sorted_view(p), p->ev, beta_t, p->beta_ref, p->dbeta, images, cache, st);
-    p->cache_valid = cache != nullptr;
+    p->cache_valid = (flags & PT_CACHE) != 0;
     return launch_status("paths_reweight");
 }
 

@@ -95,8 +95,14 @@ void launch_sample(const DevScene& S, const float* beta, uint64_t first, uint64_
                    uint32_t epoch, double* images, double* tallies, uint64_t* fps, const StoreBuf* store,
                    cudaStream_t st);
 
-void launch_sort(const StoreBuf& in, uint64_t n, int n_buckets, uint32_t* blk_hist, Buckets* buckets, int n_cams,
-                 uint4* out_a, float4* out_b, cudaStream_t st);
+// counting sort of the stored paths by collision count: counts and bucket
+// offsets (readable from `buckets` when the stream reaches this point), then
+// the scatter of the records into bucket-contiguous order
+void launch_sort_count(const StoreBuf& in, uint64_t n, int n_buckets, uint32_t* blk_hist, Buckets* buckets,
+                       cudaStream_t st);
+void launch_sort_scatter(const StoreBuf& in, uint64_t n, const uint32_t* blk_hist, Buckets* buckets, uint4* out_a,
+                         float4* out_b, cudaStream_t st);
+uint64_t sort_blocks(uint64_t n);   // blocks of the counting sort (rows of blk_hist)
 
 void launch_events(const DevScene& S, const SortedPaths& P, const Events& E, cudaStream_t st);
 

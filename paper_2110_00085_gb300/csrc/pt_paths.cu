@@ -219,14 +219,21 @@ unsigned blocks_for(uint64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); 
 
 }  // namespace
 
-void launch_sort(const StoreBuf& in, uint64_t n, int n_buckets, uint32_t* blk_hist, Buckets* buckets, int n_cams,
-                 uint4* out_a, float4* out_b, cudaStream_t st) {
+void launch_sort_count(const StoreBuf& in, uint64_t n, int n_buckets, uint32_t* blk_hist, Buckets* buckets,
+                       cudaStream_t st) {
     const uint32_t nblk = blocks_for(n, kSortThreads);
     k_sort_count<<<nblk, kSortThreads, 0, st>>>(in.cnt, n, blk_hist, nblk);
     k_sort_scan<<<kBuckets, 1024, 0, st>>>(blk_hist, nblk, buckets);
     k_bucket_offsets<<<1, 32, 0, st>>>(buckets, n_buckets);
+}
+
+void launch_sort_scatter(const StoreBuf& in, uint64_t n, const uint32_t* blk_hist, Buckets* buckets, uint4* out_a,
+                         float4* out_b, cudaStream_t st) {
+    const uint32_t nblk = blocks_for(n, kSortThreads);
     k_sort_scatter<<<nblk, kSortThreads, 0, st>>>(in, n, blk_hist, nblk, buckets, out_a, out_b);
 }
+
+uint64_t sort_blocks(uint64_t n) { return blocks_for(n, kSortThreads); }
 
 void launch_grad_reference(const DevScene& S, const SortedPaths& P, const float* beta_t, const float* beta_ref,
                            const float* dbeta, const double* dldi, double* grad, cudaStream_t st) {

@@ -26,6 +26,69 @@ LAUNCHES = {"store": 10, "reweight": 3, "residual": 1, "grad_cache": 2, "grad": 
             "adam_counted": 2}
 
 
+MAX_CHUNK = 1 << 26   # paths per stored-path handle in ChunkedPaths
+
+
+class ChunkedPaths:
+    """A path set too large for one stored-path handle, kept as handles over
+    contiguous ranges of path ids, each normalised by the total count; the
+    calls of native.Paths run chunk after chunk, the first writing the
+    images / gradient and the others accumulating into them.  The Philox
+    streams depend on the path id only, so the result is the single-handle
+    result up to the order of the FP64 additions."""
+
+    def __init__(self, scene: N.Scene, chunk: int = MAX_CHUNK):
+        self.scene = scene
+        self.chunk = int(chunk)
+        self.parts = []
+
+    def store(self, beta, n_paths: int, seed: int, epoch: int = 0, images_ref=None, tallies=None,
+              fingerprints=None):
+        n = int(n_paths)
+        k = (n + self.chunk - 1) // self.chunk
+        while len(self.parts) < k:
+            self.parts.append(N.Paths(self.scene))
+        while len(self.parts) > k:
+            self.parts.pop().close()
+        for i, p in enumerate(self.parts):
+            first = i * self.chunk
+            m = min(self.chunk, n - first)
+            p.store(beta, m, seed, first=first, n_norm=n, epoch=epoch, images_ref=images_ref, accumulate=i > 0,
+                    tallies=tallies, fingerprints=None if fingerprints is None else fingerprints[first:first + m])
+        return self
+
+    def reweight(self, beta_t, images=None, cache: bool = False, accumulate: bool = False):
+        if images is None:
+            images = self.scene.new_images()
+        for i, p in enumerate(self.parts):
+            p.reweight(beta_t, images, cache=cache, accumulate=accumulate or i > 0)
+        return images
+
+    def grad(self, beta_t, dldi, grad=None, cache: bool = False, accumulate: bool = False):
+        if grad is None:
+            grad = torch.zeros(self.scene.n_voxels, dtype=torch.float64, device=dldi.device)
+        for i, p in enumerate(self.parts):
+            p.grad(beta_t, dldi, grad, cache=cache, accumulate=accumulate or i > 0)
+        return grad
+
+    def info(self) -> dict:
+        out = None
+        for p in self.parts:
+            d = p.info()
+            if out is None:
+                out = d
+            else:
+                for key in ("n_paths", "n_stored", "n_records", "bytes_device"):
+                    out[key] += d[key]
+                out["bucket"] = [a + b for a, b in zip(out["bucket"], d["bucket"])]
+        return out
+
+    def close(self):
+        for p in self.parts:
+            p.close()
+        self.parts = []
+
+
 class Reconstruction:
     def __init__(self, scene: N.Scene, gt_images: torch.Tensor, beta0: torch.Tensor, n_paths: int,
                  n_r: int = 10, lr: float = 1.0, seed: int = 1234, cache: bool = True,
@@ -40,7 +103,8 @@ class Reconstruction:
         self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps
         self.seed = int(seed)
         self.cache = cache
-        self.paths = N.Paths(scene)
+        # one handle up to MAX_CHUNK paths, chunked handles above
+        self.paths = N.Paths(scene) if self.n_paths <= MAX_CHUNK else ChunkedPaths(scene)
         self.images = scene.new_images()
         self.dldi = torch.zeros_like(self.images)
         self.grad = torch.zeros(scene.n_voxels, dtype=torch.float64, device=self.beta.device)
@@ -52,7 +116,10 @@ class Reconstruction:
     def resample(self):
         self.paths.store(self.beta, self.n_paths, self.seed, epoch=self.epoch)
         self.epoch += 1
-        self.launches += LAUNCHES["store"]
+        self.launches += LAUNCHES["store"] * self._parts()
+
+    def _parts(self) -> int:
+        return len(self.paths.parts) if isinstance(self.paths, ChunkedPaths) else 1
 
     def step(self, timers=None):
         """One Adam step; ``timers`` (optional dict name -> list) receives
@@ -77,8 +144,8 @@ class Reconstruction:
         if timers is not None:
             timers.setdefault("render_grad", []).append((a, ev()))
         N.adam_step(self.beta, self.m, self.v, self.grad, self.t + 1, self.lr, self.b1, self.b2, self.eps)
-        self.launches += LAUNCHES["reweight"] + LAUNCHES["residual"] + LAUNCHES["adam"] + (
-            LAUNCHES["grad_cache"] if self.cache else LAUNCHES["grad"])
+        self.launches += self._parts() * (LAUNCHES["reweight"] + (
+            LAUNCHES["grad_cache"] if self.cache else LAUNCHES["grad"])) + LAUNCHES["residual"] + LAUNCHES["adam"]
         self.t += 1
 
 

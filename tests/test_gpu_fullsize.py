@@ -149,7 +149,8 @@ def test_fullsize_invariants(full_run):
     assert abs(lhs - rhs) < 1e-5 * lhs
     info = full_run["info"]
     bk = info["bucket"]
-    assert sum(bk) == int(T["entered"])
+    w0 = T["injected"] / T["entered"]     # paths that miss the box hold no collisions
+    assert sum(bk) == FULL and int(T["entered"]) + round(T["missed"] / w0) == FULL
     assert sum(k * c for k, c in enumerate(bk)) == int(T["collisions"])
     assert info["n_records"] == sum((k + 1) * c for k, c in enumerate(bk) if k >= 1)
 
@@ -198,3 +199,70 @@ def test_batch_fullsize_matches_per_scene_calls_and_oracle_fingerprints():
             o = O.render(sc, br[k], first=int(pid), n=1, n_norm=sc.n_paths, fingerprints=True, scene_id=k)
             bad += int(o["fingerprints"][0] != fps[k][pid])
     assert bad <= 1
+
+
+def test_cumulus256_chunked_fullsize():
+    """The large reconstruction at full size (256^3 fractal cumulus in air,
+    21 cameras of 256x256, 2^28 paths), stored as four chunks of 2^26 path
+    ids: fingerprints of sampled ids across all chunks and single-path
+    stores match the oracle; reweighting at beta_ref gives the store's own
+    images; the tallies balance energy and match the buckets."""
+    from paper_2110_00085_gb300.driver import ChunkedPaths
+    n = 1 << 28
+    sc = synth.config(5, n_paths=n)
+    scene = N.Scene(sc)
+    rng = np.random.default_rng(55)
+    br = sc.beta_cloud.astype(np.float32)
+    bt = (sc.beta_cloud * rng.uniform(0.9, 1.15, size=sc.beta_cloud.shape)).astype(np.float32)
+    dl = rng.standard_normal(scene.n_pixels)
+    cp = ChunkedPaths(scene)
+    fp = torch.zeros(n, dtype=torch.int64, device="cuda")
+    tal = torch.zeros(N.TALLY_COUNT, dtype=torch.float64, device="cuda")
+    ref = scene.new_images()
+    cp.store(t32(br), n, sc.seed, images_ref=ref, tallies=tal, fingerprints=fp)
+    assert len(cp.parts) == 4
+    same = cp.reweight(t32(br), cache=False)
+    img = cp.reweight(t32(bt), cache=True)
+    g = cp.grad(t32(bt), t64(dl), cache=True)
+    torch.cuda.synchronize()
+    scene.check()
+    info = cp.info()
+    cp.close()
+    assert np.abs(img.cpu().numpy()).max() > 0 and np.abs(g.cpu().numpy()).max() > 0
+    assert torch.allclose(same, ref, rtol=1e-11, atol=0)
+    T = dict(zip(N.TALLY_NAMES, tal.cpu().numpy()))
+    assert abs(T["injected"] + T["rr_gain"] - T["escaped"] - T["absorbed"] - T["truncated"] - T["rr_killed"]) \
+        < 1e-5 * T["injected"]
+    # every path has a bucket (paths that miss the box hold no collisions)
+    bk = info["bucket"]
+    w0 = T["injected"] / T["entered"]
+    assert sum(bk) == n and int(T["entered"]) + round(T["missed"] / w0) == n
+    assert sum(k * c for k, c in enumerate(bk)) == int(T["collisions"])
+    fph = fp.cpu().numpy().view(np.uint64)
+    del fp
+    ids = [int(i) for i in rng.integers(0, n, 60)] + [0, (1 << 26) - 1, 1 << 26, n - 1]
+    bad = sum(int(O.render(sc, br, first=pid, n=1, n_norm=n, fingerprints=True)["fingerprints"][0] != fph[pid])
+              for pid in ids)
+    assert bad <= 1
+    # single-path stores of sampled ids against the oracle, element by element
+    gi = scene.new_images()
+    gg = torch.zeros(scene.n_voxels, dtype=torch.float64, device="cuda")
+    oi = np.zeros(scene.n_pixels); icond = np.zeros(scene.n_pixels)
+    og = np.zeros(scene.n_voxels); oabs = np.zeros(scene.n_voxels); ocond = np.zeros(scene.n_voxels)
+    used = 0
+    for pid in ids[:12] + [n - 1]:
+        o = O.render(sc, br, bt, first=pid, n=1, n_norm=n, dldi=dl, grad_abs=True, grad_cond=True,
+                     image_cond=True, fingerprints=True)
+        if o["fingerprints"][0] != fph[pid]:
+            continue
+        one = N.Paths(scene).store(t32(br), 1, sc.seed, first=pid, n_norm=n)
+        one.reweight(t32(bt), gi, cache=True, accumulate=True)
+        one.grad(t32(bt), t64(dl), gg, cache=True, accumulate=True)
+        one.close()
+        oi += o["images"]; icond += o["image_cond"]
+        og += o["grad"]; oabs += o["grad_abs"]; ocond += o["grad_cond"]
+        used += 1
+    torch.cuda.synchronize()
+    assert used >= 11 and np.abs(oi).max() > 0
+    assert_images_close(gi.cpu().numpy(), oi, cond=icond, what="cumulus256 sampled paths, images")
+    assert_grad_close(gg.cpu().numpy(), og, oabs, ocond, what="cumulus256 sampled paths, gradient")
