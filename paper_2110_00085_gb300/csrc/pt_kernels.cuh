@@ -27,8 +27,9 @@ struct Buckets {
 };
 
 // Collision vertices ("events") of the stored paths, binned by the Morton
-// code of their 2x2x2-voxel block: neighbouring events share a warp, so
-// their shadow rays to a camera start together and run side by side.
+// code of their voxel and, with spare bits, of their position inside it:
+// neighbouring events share a warp, so their shadow rays to a camera start
+// together and run side by side.
 struct Events {
     uint4* a;          // {x, y, z bits, packed voxel}
     float4* b;         // {incoming direction, W: path weight before the vertex}
