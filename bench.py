@@ -268,11 +268,25 @@ def run_batch(args, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def kernel_source_hash() -> str:
+    """SHA-1 (16 hex digits) of the event kernels' code: their sources with
+    comments and blank space removed, so that only a change of code counts."""
+    import hashlib
+    import re
+    here = os.path.dirname(os.path.abspath(__file__))
+    h = hashlib.sha1()
+    for f in ("pt_event_ops.cuh", "pt_events.cu", "pt_device.cuh", "pt_kernels.cuh"):
+        src = open(os.path.join(here, "paper_2110_00085_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(call, n):
     """DRAM bytes per call of ``call`` from the committed ncu record, scaled
     to n paths; None unless the kernel sources still hash to the profiled
     ones (a changed kernel has no counters yet)."""
-    import hashlib
     here = os.path.dirname(os.path.abspath(__file__))
     path = os.path.join(here, "profiles", f"traffic_{call}_noise128.txt")
     if not os.path.exists(path):
@@ -283,10 +297,7 @@ def profiled_traffic(call, n):
         if line and not line.startswith("#") and "=" in line:
             k, v = line.split("=", 1)
             rec[k.strip()] = v.strip()
-    h = hashlib.sha1()
-    for f in ("pt_event_ops.cuh", "pt_events.cu", "pt_device.cuh", "pt_kernels.cuh"):
-        h.update(open(os.path.join(here, "paper_2110_00085_gb300", "csrc", f), "rb").read())
-    if rec.get("call") != call or rec.get("source_sha1_16") != h.hexdigest()[:16]:
+    if rec.get("call") != call or rec.get("source_sha1_16") != kernel_source_hash():
         return None
     return float(rec["bytes_per_call"]) * n / float(rec["paths"])
 
