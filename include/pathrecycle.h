@@ -195,10 +195,12 @@ int paths_info(const pt_paths* paths, pt_paths_info* out, void* stream);
  * eps, step number t >= 1) on the cloud extinction with the projection
  * beta >= 0 (Sec. 6: a modified Adam; the modification is not given, the
  * projection keeps extinction physical).  beta, m, v: device float32[n];
- * grad: device float64[n].
+ * grad: device float64[n]; mask (nullable): device uint8[n], voxels with 0
+ * keep beta, m and v (the optimisation restricted to the photo-hull of
+ * space_carve, the initialisation of Sec. 6).
  */
-int adam_step(float* beta, float* m, float* v, const double* grad, int64_t n,
-              int32_t t, float lr, float b1, float b2, float eps, void* stream);
+int adam_step(float* beta, float* m, float* v, const double* grad, const uint8_t* mask,
+              int64_t n, int32_t t, float lr, float b1, float b2, float eps, void* stream);
 
 /*
  * adam_step_counted -- adam_step with the step number kept on the device:
@@ -206,9 +208,9 @@ int adam_step(float* beta, float* m, float* v, const double* grad, int64_t n,
  * corrections (written to scratch, device float[2]).  One captured CUDA
  * graph can so replay every step.
  */
-int adam_step_counted(float* beta, float* m, float* v, const double* grad, int64_t n,
-                      int32_t* step, float* scratch, float lr, float b1, float b2, float eps,
-                      void* stream);
+int adam_step_counted(float* beta, float* m, float* v, const double* grad, const uint8_t* mask,
+                      int64_t n, int32_t* step, float* scratch, float lr, float b1, float b2,
+                      float eps, void* stream);
 
 /*
  * loss_residual -- dL_dI = images - gt and *loss = 1/2 sum (images - gt)^2
@@ -217,6 +219,18 @@ int adam_step_counted(float* beta, float* m, float* v, const double* grad, int64
  */
 int loss_residual(const double* images, const double* gt, int64_t n,
                   double* dL_dI, double* loss, void* stream);
+
+/*
+ * space_carve -- photo-hull of a cloud from its images (space carving,
+ * Kutulakos & Seitz 2000), the initialisation of the reconstructions of
+ * Sec. 6.  images: device float64, camera-major as render_forward's.
+ * mask: device, V bytes (x fastest), 1 = voxel kept.  A voxel is kept
+ * unless some camera sees its centre on a clear pixel (radiance <=
+ * threshold); a camera that does not see the centre has no say.  The
+ * centre and its projection are computed in float32.
+ */
+int space_carve(const pt_scene* scene, const double* images, double threshold,
+                uint8_t* mask, void* stream);
 
 /*
  * Batches: many scenes (each with its own grid size, cameras and stored

@@ -95,6 +95,9 @@ def lib():
             L.or_sun_rect.argtypes = [C.POINTER(ORScene), _dp]
             L.or_single_scatter_quad.argtypes = [C.POINTER(ORScene), _fp, C.c_int, C.c_int, _dp]
             L.or_camera_frame.argtypes = [C.POINTER(ORScene), C.c_int, _dp]
+            L.or_space_carve.argtypes = [C.POINTER(ORScene), _dp, C.c_double, C.POINTER(C.c_uint8)]
+            L.or_pixel_coords.argtypes = [C.POINTER(ORScene), C.c_int, _dp, _dp]
+            L.or_pixel_coords.restype = C.c_int
             L.or_tally_count.restype = C.c_int
             _lib = L
     return _lib
@@ -323,3 +326,22 @@ def adam_step(beta, m, v, grad, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     vh = v / (1 - b2 ** t)
     beta = np.maximum(beta - lr * mh / (np.sqrt(vh) + eps), 0.0)
     return beta, m, v
+
+
+def space_carve(sc, images, threshold: float) -> np.ndarray:
+    """Photo-hull mask (V uint8, x fastest; 1 = kept) of ``images``
+    (camera-major, as render_forward's), see or_space_carve."""
+    os_ = OScene(sc)
+    im = np.ascontiguousarray(np.asarray(images, dtype=np.float64).reshape(-1))
+    mask = np.zeros(os_.n_voxels, dtype=np.uint8)
+    lib().or_space_carve(os_.ref, _ptr(im, _dp), float(threshold), mask.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return mask
+
+
+def pixel_coords(sc, cam: int, x):
+    """Continuous (column, row) of point x in camera ``cam``, None if behind."""
+    os_ = OScene(sc)
+    p = np.asarray(x, dtype=np.float64).copy()
+    out = np.zeros(2)
+    ok = lib().or_pixel_coords(os_.ref, int(cam), _ptr(p, _dp), _ptr(out, _dp))
+    return out if ok else None

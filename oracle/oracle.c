@@ -978,6 +978,53 @@ int or_render(const or_scene* s, const float* beta_ref, const float* beta_t,
     return err;
 }
 
+/*
+ * Space carving (Kutulakos & Seitz, IJCV 2000), the initialisation of the
+ * reconstructions of Sec. 6: the photo-hull of the cloud from its images.
+ * READING (the paper names the method only): a voxel stays in the hull
+ * unless some camera sees its centre on a clear pixel (radiance at or below
+ * threshold); a camera whose image does not contain the centre, or that has
+ * it behind, has no say.  images: camera-major, as render_forward's.
+ * mask: V bytes, 1 = in the hull.
+ */
+void or_space_carve(const or_scene* s, const double* images, double threshold, uint8_t* mask)
+{
+    ocam* cams = (ocam*)malloc(sizeof(ocam) * (size_t)(s->n_cams > 0 ? s->n_cams : 1));
+    setup_cams(s, cams);
+    for (int iz = 0; iz < s->nz; ++iz)
+        for (int iy = 0; iy < s->ny; ++iy)
+            for (int ix = 0; ix < s->nx; ++ix) {
+                const double x[3] = {s->origin[0] + (ix + 0.5) * s->voxel, s->origin[1] + (iy + 0.5) * s->voxel,
+                                     s->origin[2] + (iz + 0.5) * s->voxel};
+                uint8_t keep = 1;
+                for (int d = 0; d < s->n_cams && keep; ++d) {
+                    int col, row;
+                    const int64_t pix = project(&cams[d], x, &col, &row);
+                    if (pix >= 0 && images[cams[d].off + pix] <= threshold) keep = 0;
+                }
+                mask[ix + (int64_t)s->nx * (iy + (int64_t)s->ny * iz)] = keep;
+            }
+    free(cams);
+}
+
+/* continuous image coordinates (column, row; pixel (c, r) covers [c, c+1) x
+ * [r, r+1)) of point x in camera cam; returns 0 when x is behind it */
+int or_pixel_coords(const or_scene* s, int cam, const double x[3], double out[2])
+{
+    ocam* cams = (ocam*)malloc(sizeof(ocam) * (size_t)(s->n_cams > 0 ? s->n_cams : 1));
+    setup_cams(s, cams);
+    const ocam* k = &cams[cam];
+    const double q[3] = {x[0] - k->C[0], x[1] - k->C[1], x[2] - k->C[2]};
+    const double z = dot3(q, k->F);
+    int ok = z > 0.0;
+    if (ok) {
+        out[0] = (dot3(q, k->R) / (z * k->tx) + 1.0) * 0.5 * k->W;
+        out[1] = (1.0 - dot3(q, k->U) / (z * k->ty)) * 0.5 * k->H;
+    }
+    free(cams);
+    return ok;
+}
+
 /* Vertices of one path, for inspection: returns B; x (3*(B+1)), om, v, l */
 int or_path(const or_scene* s, const float* beta, uint64_t pid, double* x, double* om, int64_t* v, double* l, int* end)
 {

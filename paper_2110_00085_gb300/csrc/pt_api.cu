@@ -63,6 +63,23 @@ __global__ void k_pixel_omega(const DevCam* cams, int n_cams, const double* tans
     omega[g] = (float)(F(xb, yb) - F(xa, yb) - F(xb, ya) + F(xa, ya));
 }
 
+// photo-hull: a voxel stays unless some camera sees its centre on a clear
+// pixel (radiance <= thr); cameras that do not see the centre have no say
+__global__ void k_space_carve(DevScene S, const double* __restrict__ images, double thr,
+                              uint8_t* __restrict__ mask) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < S.V; v += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(v % S.nx), iy = (int)((v / S.nx) % S.ny), iz = (int)(v / ((int64_t)S.nx * S.ny));
+        const float3 x = make_float3(fmaf((float)ix + 0.5f, S.vox, S.ox), fmaf((float)iy + 0.5f, S.vox, S.oy),
+                                     fmaf((float)iz + 0.5f, S.vox, S.oz));
+        uint8_t keep = 1;
+        for (int c = 0; c < S.n_cams && keep; ++c) {
+            const Proj q = project(S.cams[c], x);
+            if (q.pix >= 0 && images[S.cams[c].off + q.pix] <= thr) keep = 0;
+        }
+        mask[v] = keep;
+    }
+}
+
 __global__ void k_resid(const double* __restrict__ img, const double* __restrict__ gt, int64_t n,
                         double* __restrict__ r, double* __restrict__ loss) {
     __shared__ double part[256];
@@ -81,10 +98,12 @@ __global__ void k_resid(const double* __restrict__ img, const double* __restrict
     if (threadIdx.x == 0 && loss) atomicAdd(loss, 0.5 * part[0]);
 }
 
+// voxels with mask[i] == 0 (mask non-null) keep beta, m and v
 __global__ void k_adam(float* __restrict__ beta, float* __restrict__ m, float* __restrict__ v,
-                       const double* __restrict__ g, int64_t n, float lr, float b1, float b2, float eps,
-                       float inv_bc1, float inv_bc2) {
+                       const double* __restrict__ g, const uint8_t* __restrict__ mask, int64_t n, float lr, float b1,
+                       float b2, float eps, float inv_bc1, float inv_bc2) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (mask && !mask[i]) continue;
         const float gi = __double2float_rn(g[i]);
         const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
         const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
@@ -104,10 +123,11 @@ __global__ void k_adam_count(int32_t* step, float b1, float b2, float* inv_bc) {
 }
 
 __global__ void k_adam_dev(float* __restrict__ beta, float* __restrict__ m, float* __restrict__ v,
-                           const double* __restrict__ g, int64_t n, float lr, float b1, float b2, float eps,
-                           const float* __restrict__ inv_bc) {
+                           const double* __restrict__ g, const uint8_t* __restrict__ mask, int64_t n, float lr,
+                           float b1, float b2, float eps, const float* __restrict__ inv_bc) {
     const float inv_bc1 = inv_bc[0], inv_bc2 = inv_bc[1];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (mask && !mask[i]) continue;
         const float gi = __double2float_rn(g[i]);
         const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
         const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
@@ -605,24 +625,24 @@ int paths_info(const pt_paths* p, pt_paths_info* out, void* stream) {
     return PT_OK;
 }
 
-int adam_step(float* beta, float* m, float* v, const double* grad, int64_t n, int32_t t, float lr, float b1, float b2,
-              float eps, void* stream) {
+int adam_step(float* beta, float* m, float* v, const double* grad, const uint8_t* mask, int64_t n, int32_t t,
+              float lr, float b1, float b2, float eps, void* stream) {
     if (!beta || !m || !v || !grad || n < 0 || t < 1) return fail(PT_E_INVALID, "adam_step: bad argument");
     if (n == 0) return PT_OK;
     const double bc1 = 1.0 - std::pow((double)b1, (double)t);
     const double bc2 = 1.0 - std::pow((double)b2, (double)t);
-    k_adam<<<grid_for(n, 256), 256, 0, S_(stream)>>>(beta, m, v, grad, n, lr, b1, b2, eps, (float)(1.0 / bc1),
-                                                      (float)(1.0 / bc2));
+    k_adam<<<grid_for(n, 256), 256, 0, S_(stream)>>>(beta, m, v, grad, mask, n, lr, b1, b2, eps,
+                                                      (float)(1.0 / bc1), (float)(1.0 / bc2));
     return launch_status("adam_step");
 }
 
-int adam_step_counted(float* beta, float* m, float* v, const double* grad, int64_t n, int32_t* step,
-                      float* scratch, float lr, float b1, float b2, float eps, void* stream) {
+int adam_step_counted(float* beta, float* m, float* v, const double* grad, const uint8_t* mask, int64_t n,
+                      int32_t* step, float* scratch, float lr, float b1, float b2, float eps, void* stream) {
     if (!beta || !m || !v || !grad || !step || !scratch || n < 0)
         return fail(PT_E_INVALID, "adam_step_counted: bad argument");
     cudaStream_t st = S_(stream);
     k_adam_count<<<1, 32, 0, st>>>(step, b1, b2, scratch);
-    if (n > 0) k_adam_dev<<<grid_for(n, 256), 256, 0, st>>>(beta, m, v, grad, n, lr, b1, b2, eps, scratch);
+    if (n > 0) k_adam_dev<<<grid_for(n, 256), 256, 0, st>>>(beta, m, v, grad, mask, n, lr, b1, b2, eps, scratch);
     return launch_status("adam_step_counted");
 }
 
@@ -633,6 +653,13 @@ int loss_residual(const double* images, const double* gt, int64_t n, double* dld
     if (n == 0) return PT_OK;
     k_resid<<<grid_for(n, 256, 152 * 4), 256, 0, st>>>(images, gt, n, dldi, loss);
     return launch_status("loss_residual");
+}
+
+int space_carve(const pt_scene* sc, const double* images, double threshold, uint8_t* mask, void* stream) {
+    if (!sc || !images || !mask) return fail(PT_E_INVALID, "space_carve: null argument");
+    cudaStream_t st = S_(stream);
+    k_space_carve<<<grid_for(sc->ds.V, 256), 256, 0, st>>>(sc->ds, images, threshold, mask);
+    return launch_status("space_carve");
 }
 
 // ------------------------------------------------------------ batches --

@@ -78,10 +78,11 @@ def load():
         L.render_grad.argtypes = [_vp, _vp, _vp, _vp, _u32, _vp]
         L.paths_free.argtypes = [_vp]
         L.paths_info.argtypes = [_vp, C.POINTER(PtPathsInfo), _vp]
-        L.adam_step.argtypes = [_vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.c_float, C.c_float, C.c_float,
+        L.adam_step.argtypes = [_vp, _vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.c_float, C.c_float, C.c_float,
                                 C.c_float, _vp]
         L.loss_residual.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
-        L.adam_step_counted.argtypes = [_vp, _vp, _vp, _vp, C.c_int64, _vp, _vp, C.c_float, C.c_float, C.c_float,
+        L.space_carve.argtypes = [_vp, _vp, C.c_double, _vp, _vp]
+        L.adam_step_counted.argtypes = [_vp, _vp, _vp, _vp, _vp, C.c_int64, _vp, _vp, C.c_float, C.c_float, C.c_float,
                                         C.c_float, _vp]
         L.pt_check.argtypes = [_vp, _vp]
         L.render_forward_static.argtypes = [C.POINTER(PtSceneDesc), _vp, _u64, _u64, C.c_double, _u64, _u32,
@@ -188,6 +189,16 @@ class Scene:
     def check(self, stream=None):
         _check(load().pt_check(self._h, _vp(_stream(stream))), "pt_check")
 
+    def space_carve(self, images: torch.Tensor, threshold: float, mask: Optional[torch.Tensor] = None,
+                    stream=None) -> torch.Tensor:
+        """Photo-hull mask (uint8, 1 = kept) of the cloud seen in ``images``."""
+        if mask is None:
+            mask = torch.empty(self.n_voxels, dtype=torch.uint8, device="cuda")
+        rc = load().space_carve(self._h, _dev(images, torch.float64, "images", self.n_pixels), float(threshold),
+                                _dev(mask, torch.uint8, "mask", self.n_voxels), _vp(_stream(stream)))
+        _check(rc, "space_carve")
+        return mask
+
     def render_forward(self, beta: torch.Tensor, n_paths: int, seed: int, first: int = 0, n_norm=None,
                        epoch: int = 0, images: Optional[torch.Tensor] = None, accumulate: bool = False,
                        tallies: Optional[torch.Tensor] = None, fingerprints: Optional[torch.Tensor] = None,
@@ -270,20 +281,23 @@ class Paths:
 
 
 def adam_step(beta, m, v, grad, t: int, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8,
-              stream=None):
+              mask=None, stream=None):
+    """Adam + projection beta >= 0; ``mask`` (uint8, optional): voxels with 0 stay."""
     n = beta.numel()
     rc = load().adam_step(_dev(beta, torch.float32, "beta"), _dev(m, torch.float32, "m", n),
-                          _dev(v, torch.float32, "v", n), _dev(grad, torch.float64, "grad", n), n, int(t),
+                          _dev(v, torch.float32, "v", n), _dev(grad, torch.float64, "grad", n),
+                          _opt(mask, torch.uint8, "mask", n), n, int(t),
                           float(lr), float(b1), float(b2), float(eps), _vp(_stream(stream)))
     _check(rc, "adam_step")
 
 
 def adam_step_counted(beta, m, v, grad, step, scratch, lr: float, b1: float = 0.9, b2: float = 0.999,
-                      eps: float = 1e-8, stream=None):
+                      eps: float = 1e-8, mask=None, stream=None):
     """Adam with the step number in device memory (``step``: int32[1])."""
     n = beta.numel()
     rc = load().adam_step_counted(_dev(beta, torch.float32, "beta"), _dev(m, torch.float32, "m", n),
-                                  _dev(v, torch.float32, "v", n), _dev(grad, torch.float64, "grad", n), n,
+                                  _dev(v, torch.float32, "v", n), _dev(grad, torch.float64, "grad", n),
+                                  _opt(mask, torch.uint8, "mask", n), n,
                                   _dev(step, torch.int32, "step", 1), _dev(scratch, torch.float32, "scratch", 2),
                                   float(lr), float(b1), float(b2), float(eps), _vp(_stream(stream)))
     _check(rc, "adam_step_counted")

@@ -43,7 +43,7 @@ def test_null_arguments_are_rejected_without_a_gpu():
     assert L.pt_scene_create(None, None) == 1
     assert L.paths_reweight(None, None, None, 0, None) == 1
     assert L.render_grad(None, None, None, None, 0, None) == 1
-    assert L.adam_step(None, None, None, None, 0, 0, 0.0, 0.0, 0.0, 0.0, None) == 1
+    assert L.adam_step(None, None, None, None, None, 0, 0, 0.0, 0.0, 0.0, 0.0, None) == 1
 
 
 def test_scene_descriptor_validation_runs_on_host():

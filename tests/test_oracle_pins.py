@@ -439,3 +439,40 @@ def test_image_budget_is_measured_not_injected():
     k = 2 * 40 * 40 + 788      # camera 2: the local estimate of its 4th collision
     assert one["images"][k] > 0
     assert one["image_cond"][k] > 100 * np.median(ic[lit] / im[lit]) * one["images"][k]
+
+
+# ------------------------------------------------------------ space carving --
+def test_space_carving_limits_and_monotonicity():
+    """Photo-hull of the initialisation (Sec. 6): all-cloudy images keep
+    every voxel, all-clear ones carve every voxel (each camera's field of
+    view holds the whole box); a higher threshold and an extra camera can
+    only carve more."""
+    sc = synth.config(1, n_paths=16)
+    npx = sum(c.width * c.height for c in sc.cameras)
+    V = int(np.prod(sc.n))
+    assert O.space_carve(sc, np.ones(npx), 0.5).sum() == V
+    assert O.space_carve(sc, np.zeros(npx), 0.0).sum() == 0
+    img = O.single_scatter_quad(sc.replace(max_orders=1), sc.beta_cloud, sub=4, steps=2)
+    lo = O.space_carve(sc, img, 0.02 * img.max())
+    hi = O.space_carve(sc, img, 0.2 * img.max())
+    assert hi.sum() < lo.sum() and not np.any(hi & ~lo)
+    few = sc.replace(cameras=sc.cameras[:4])
+    m4 = O.space_carve(few, img[: sum(c.width * c.height for c in few.cameras)], 0.02 * img.max())
+    assert not np.any(lo & ~m4) and m4.sum() > lo.sum()
+
+
+def test_space_carving_keeps_the_cloud_of_single_scatter_images():
+    """Images of the deterministic single-scattering quadrature (independent
+    of the carving code) of a blob cloud without air, carved at threshold 0:
+    every voxel with extinction is kept (its own line of sight to each
+    camera crosses cloud, lit by the sun), and the hull is much smaller than
+    the grid."""
+    sc = synth.config(1, n_paths=16)
+    beta = sc.beta_cloud.copy()
+    beta[beta < 0.05 * beta.max()] = 0.0          # a cloud with an edge
+    img = O.single_scatter_quad(sc.replace(max_orders=1), beta, sub=8, steps=2)
+    mask = O.space_carve(sc, img, 0.0)
+    cloud = beta.reshape(-1) > 0
+    assert cloud.any()
+    assert np.all(mask[cloud] == 1)
+    assert mask.sum() < 0.5 * mask.size
