@@ -189,6 +189,22 @@ class Reconstruction:
             2 if self.decorrelate else 1) + LAUNCHES["adam"]
         self.t += 1
 
+    def snapshot(self) -> dict:
+        """Optimisation state (extinction, Adam moments, step and resample
+        counters), for checkpoint / resume."""
+        return {"beta": self.beta.clone(), "m": self.m.clone(), "v": self.v.clone(), "t": self.t,
+                "epoch": self.epoch}
+
+    def restore(self, snap: dict):
+        """Back to a snapshot (tensors copied in place).  From a snapshot
+        taken at a resample boundary (t mod N_r == 0) the next steps repeat
+        exactly: the resample draws the same paths (same seeds and epoch)."""
+        self.beta.copy_(snap["beta"])
+        self.m.copy_(snap["m"])
+        self.v.copy_(snap["v"])
+        self.t = snap["t"]
+        self.epoch = snap["epoch"]
+
     def close(self):
         self.paths.close()
         if self.paths_b is not None:

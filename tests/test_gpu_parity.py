@@ -169,6 +169,16 @@ def test_empty_medium_gives_zero():
     assert paths.reweight(z).abs().max().item() == 0.0
     g = paths.grad(z, torch.ones(scene.n_pixels, dtype=torch.float64, device="cuda"))
     assert g.abs().max().item() == 0.0
+    # the cached pass with no events at all (buffers sized from the counts)
+    assert paths.reweight(z, cache=True).abs().max().item() == 0.0
+    g = paths.grad(z, torch.ones(scene.n_pixels, dtype=torch.float64, device="cuda"), cache=True)
+    assert g.abs().max().item() == 0.0
+    # a handle reused for a larger path set grows its buffers
+    paths.store(t32(sc.beta_cloud), sc.n_paths, sc.seed)
+    img2 = paths.reweight(t32(sc.beta_cloud), cache=True)
+    ref = scene.render_forward(t32(sc.beta_cloud), sc.n_paths, sc.seed)
+    torch.cuda.synchronize()
+    assert torch.allclose(img2, ref, rtol=1e-11, atol=0)
 
 
 def test_single_path_and_first_order_only():

@@ -125,3 +125,28 @@ def test_coarse_to_fine_reconstruction_moves_toward_the_truth():
     assert all(np.isfinite([h["loss"], h["eps"], h["delta"]]).all() for h in hist)
     assert np.all(c2f.rec.beta.cpu().numpy()[~hull] == 0.0)
     assert hist[-1]["eps"] < eps0 and abs(hist[-1]["delta"]) < abs(delta0)
+
+
+def test_reconstruction_checkpoint_resume_repeats_steps():
+    """A snapshot taken at a resample boundary and restored repeats the same
+    Adam steps (same paths: seeds and epoch come back with it)."""
+    from paper_2110_00085_gb300.driver import Reconstruction
+    sc = synth.config(1, n_paths=1 << 14)
+    scene = N.Scene(sc)
+    bt = torch.from_numpy(sc.beta_cloud.reshape(-1).astype(np.float32)).cuda()
+    gt = scene.render_forward(bt, 1 << 15, 999)
+    rec = Reconstruction(scene, gt, bt * 0.8, 1 << 14, n_r=3, lr=0.1, seed=5, decorrelate=True)
+    for _ in range(3):
+        rec.step()
+    snap = rec.snapshot()
+    for _ in range(4):
+        rec.step()
+    torch.cuda.synchronize()
+    a, la = rec.beta.clone(), float(rec.loss)
+    rec.restore(snap)
+    for _ in range(4):
+        rec.step()
+    torch.cuda.synchronize()
+    assert torch.allclose(rec.beta, a, rtol=1e-5, atol=1e-6) and abs(float(rec.loss) - la) <= 1e-9 * abs(la)
+    assert not torch.equal(snap["beta"], a)
+    rec.close()
