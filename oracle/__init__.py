@@ -55,6 +55,19 @@ class ORScene(C.Structure):
     ]
 
 
+class ORSurf(C.Structure):
+    _fields_ = [
+        ("n_spheres", C.c_int32), ("phong", C.c_int32), ("max_orders", C.c_int32), ("rr_start", C.c_int32),
+        ("epoch", C.c_uint32), ("pad", C.c_uint32),
+        ("seed", C.c_uint64),
+        ("rr_q", C.c_double),
+        ("light", C.c_double * 4),
+        ("radiance", C.c_double),
+        ("spheres", C.POINTER(C.c_double)),
+        ("cam", C.c_double * 12),
+    ]
+
+
 _dp = C.POINTER(C.c_double)
 _fp = C.POINTER(C.c_float)
 _u64p = C.POINTER(C.c_uint64)
@@ -95,6 +108,9 @@ def lib():
             L.or_sun_rect.argtypes = [C.POINTER(ORScene), _dp]
             L.or_single_scatter_quad.argtypes = [C.POINTER(ORScene), _fp, C.c_int, C.c_int, _dp]
             L.or_camera_frame.argtypes = [C.POINTER(ORScene), C.c_int, _dp]
+            L.or_surf_render.argtypes = [C.POINTER(ORSurf), C.c_double, C.c_double, C.c_uint64, C.c_uint64,
+                                         C.c_double, _dp, _dp, _dp, _dp, _dp, _u64p]
+            L.or_surf_render.restype = C.c_int
             L.or_space_carve.argtypes = [C.POINTER(ORScene), _dp, C.c_double, C.POINTER(C.c_uint8)]
             L.or_pixel_coords.argtypes = [C.POINTER(ORScene), C.c_int, _dp, _dp]
             L.or_pixel_coords.restype = C.c_int
@@ -345,3 +361,59 @@ def pixel_coords(sc, cam: int, x):
     out = np.zeros(2)
     ok = lib().or_pixel_coords(os_.ref, int(cam), _ptr(p, _dp), _ptr(out, _dp))
     return out if ok else None
+
+
+def _surf(ss, epoch: int = 0, seed=None):
+    sph = np.ascontiguousarray(np.asarray(ss.spheres, dtype=np.float64).reshape(-1))
+    st = ORSurf()
+    st.n_spheres = len(sph) // 4
+    st.phong = int(ss.phong)
+    st.max_orders = int(ss.max_orders)
+    st.rr_start = int(ss.rr_start)
+    st.epoch = int(epoch)
+    st.seed = int(ss.seed if seed is None else seed)
+    st.rr_q = float(ss.rr_q)
+    for i in range(4):
+        st.light[i] = float(ss.light[i])
+    st.radiance = float(ss.radiance)
+    st.spheres = sph.ctypes.data_as(C.POINTER(C.c_double))
+    c = ss.camera
+    vals = list(c.pos) + list(c.look_at) + list(c.up) + [c.fov_y, c.width, c.height]
+    for i in range(12):
+        st.cam[i] = float(vals[i])
+    return st, sph
+
+
+def surf_render(ss, kappa=None, gamma=None, first: int = 0, n=None, n_norm=None, dldi=None, grad_abs: bool = False,
+                tallies: bool = False, fingerprints: bool = False, epoch: int = 0, seed=None):
+    """Reflectometry scene ``ss`` (synth.SurfScene): paths [first, first+n)
+    evaluated under (kappa, gamma) (default: the scene's).  Returns images
+    (W*H), and when asked grad / grad_abs (2: d loss / d kappa, d gamma),
+    tallies (dict) and fingerprints."""
+    L = lib()
+    st, keep = _surf(ss, epoch, seed)
+    n = int(ss.n_paths if n is None else n)
+    n_norm = float(n if n_norm is None else n_norm)
+    kappa = float(ss.kappa if kappa is None else kappa)
+    gamma = float(ss.gamma if gamma is None else gamma)
+    img = np.zeros(ss.n_pixels)
+    out = {"images": img}
+    dl = g = ga = None
+    if dldi is not None:
+        dl = np.ascontiguousarray(np.asarray(dldi, dtype=np.float64).reshape(-1))
+        g = np.zeros(2)
+        out["grad"] = g
+        if grad_abs:
+            ga = np.zeros(2)
+            out["grad_abs"] = ga
+    tal = np.zeros(L.or_tally_count(), dtype=np.float64) if tallies else None
+    fp = np.zeros(n, dtype=np.uint64) if fingerprints else None
+    rc = L.or_surf_render(C.byref(st), kappa, gamma, C.c_uint64(first), C.c_uint64(n), n_norm, _ptr(img, _dp),
+                          _ptr(dl, _dp), _ptr(g, _dp), _ptr(ga, _dp), _ptr(tal, _dp), _ptr(fp, _u64p))
+    if rc != 0:
+        raise RuntimeError(f"or_surf_render failed ({rc})")
+    if tal is not None:
+        out["tallies"] = dict(zip(T_NAMES, tal.tolist()))
+    if fp is not None:
+        out["fingerprints"] = fp
+    return out

@@ -1136,3 +1136,234 @@ void or_camera_frame(const or_scene* s, int cam, double* out)
 }
 
 int or_tally_count(void) { return T_COUNT; }
+
+/* ======================================================================== */
+/* Reflectometry (Sec. 6): surfaces (the surface rendering equation of      */
+/* Sec. 3) in a closed box -- diffuse walls, a square Lambertian emitter in */
+/* the ceiling, diffuse spheres and one sphere with the Phong BRDF          */
+/* f_r = 1 - kappa + kappa (r . w')^gamma (Eq. phong).                      */
+/* READINGS (the paper gives the experiment, not its scene or sampler):     */
+/* - the BRDF is f_r / pi, so a diffuse surface (f_r = 1) reflects all the  */
+/*   light (no absorption); the lobe's cosine is taken between the mirror   */
+/*   direction r of the incoming propagation direction and the outgoing    */
+/*   one, clamped at 0;                                                      */
+/* - paths start on the emitter (uniform point, cosine-weighted direction   */
+/*   into the box, weight = emitted power) and make a local estimate toward */
+/*   the camera at every surface hit (as the volumetric method), with       */
+/*   cosine-weighted directions about the normal: the path pdf does not     */
+/*   depend on (kappa, gamma), so the recycled estimate is the plain one    */
+/*   evaluated under the new parameters (Eq. 19 with mu independent of M);  */
+/* - roulette and the order limit as for volumes.                           */
+/* ======================================================================== */
+typedef struct {
+    int32_t n_spheres, phong, max_orders, rr_start;
+    uint32_t epoch, pad;
+    uint64_t seed;
+    double rr_q;
+    double light[4];          /* emitter on the ceiling z = 1: x0, x1, y0, y1 */
+    double radiance;          /* emitted radiance */
+    const double* spheres;    /* n_spheres x 4: centre, radius */
+    double cam[12];           /* pos, look_at, up, fov_y, W, H */
+} or_surf;
+
+#define SURF_EPS 1e-4
+
+static void surf_draw(const or_surf* s, uint64_t path, uint32_t event, uint32_t tag, double u[4])
+{
+    uint32_t ctr[4], key[2], w[4];
+    ctr[0] = (uint32_t)path;
+    ctr[1] = (uint32_t)(path >> 32);
+    ctr[2] = (event & 0xffu) | ((tag & 0xffu) << 8) | ((s->epoch & 0xffffu) << 16);
+    ctr[3] = 0u;
+    key[0] = (uint32_t)s->seed;
+    key[1] = (uint32_t)(s->seed >> 32);
+    or_philox4x32_10(ctr, key, w);
+    for (int i = 0; i < 4; ++i) u[i] = u01(w[i]);
+}
+
+/* Phong factor f_r(c) for the lobe cosine c (clamped at 0) and its log
+ * derivatives in kappa and gamma */
+static double phong_f(double kappa, double gamma, double c) { return 1.0 - kappa + kappa * pow(fmax(c, 0.0), gamma); }
+static void phong_dlog(double kappa, double gamma, double c, double out[2])
+{
+    const double f = phong_f(kappa, gamma, c);
+    const double cg = c > 0.0 ? pow(c, gamma) : 0.0;
+    out[0] = (cg - 1.0) / f;
+    out[1] = c > 0.0 ? kappa * cg * log(c) / f : 0.0;
+}
+
+/* nearest surface along p + t d (d unit, p inside the box): returns the
+ * surface id (spheres 0..n-1, walls -1..-6 for x-, x+, y-, y+, z-, z+) and
+ * fills t and the normal facing the ray; no surface (numerically) -> -100 */
+static int surf_hit(const or_surf* s, const double p[3], const double d[3], double* t_out, double n[3])
+{
+    double best = INFINITY;
+    int id = -100;
+    for (int i = 0; i < s->n_spheres; ++i) {
+        const double* c = s->spheres + 4 * i;
+        const double oc[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
+        const double b = dot3(oc, d), cc = dot3(oc, oc) - c[3] * c[3];
+        const double disc = b * b - cc;
+        if (disc < 0.0) continue;
+        const double t = -b - sqrt(disc);
+        if (t > SURF_EPS && t < best) { best = t; id = i; }
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) continue;
+        const double t = ((d[a] > 0.0 ? 1.0 : 0.0) - p[a]) / d[a];
+        if (t > SURF_EPS && t < best) { best = t; id = -(2 * a + (d[a] > 0.0 ? 2 : 1)); }
+    }
+    if (id == -100) return id;
+    *t_out = best;
+    if (id >= 0) {
+        const double* c = s->spheres + 4 * id;
+        for (int k = 0; k < 3; ++k) n[k] = (p[k] + best * d[k] - c[k]) / c[3];
+    } else {
+        const int a = (-id - 1) / 2;
+        for (int k = 0; k < 3; ++k) n[k] = 0.0;
+        n[a] = (-id - 1) % 2 ? -1.0 : 1.0;     /* x+ wall faces -x, x- wall faces +x */
+    }
+    return id;
+}
+
+/* is the segment x -> x + r w free of spheres? */
+static int surf_visible(const or_surf* s, const double x[3], const double w[3], double r)
+{
+    for (int i = 0; i < s->n_spheres; ++i) {
+        const double* c = s->spheres + 4 * i;
+        const double oc[3] = {x[0] - c[0], x[1] - c[1], x[2] - c[2]};
+        const double b = dot3(oc, w), cc = dot3(oc, oc) - c[3] * c[3];
+        const double disc = b * b - cc;
+        if (disc < 0.0) continue;
+        const double t = -b - sqrt(disc);
+        if (t > SURF_EPS && t < r) return 0;
+    }
+    return 1;
+}
+
+/*
+ * Paths first .. first+n-1 (sampling independent of the BRDF parameters),
+ * evaluated under (kappa, gamma): images (W*H, row-major) += contributions /
+ * n_norm; with dldi, grad[2] += d loss / d (kappa, gamma) and gabs[2] the sum
+ * of the absolute values of its terms; tallies as or_render's; fingerprints
+ * (nullable): per path, FNV-1a of (surface id, pixel or -1) per hit and the
+ * end.
+ */
+int or_surf_render(const or_surf* s, double kappa, double gamma, uint64_t first, uint64_t n, double n_norm,
+                   double* images, const double* dldi, double* grad, double* gabs, double* tal, uint64_t* fp)
+{
+    or_scene tmp;
+    memset(&tmp, 0, sizeof(tmp));
+    tmp.n_cams = 1;
+    tmp.cams = s->cam;
+    ocam cam;
+    setup_cams(&tmp, &cam);
+    const double inv_norm = 1.0 / n_norm;
+    const double area = (s->light[1] - s->light[0]) * (s->light[3] - s->light[2]);
+    const double w0 = OR_PI * s->radiance * area;
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint64_t pid = first + i;
+        uint64_t h = 0xcbf29ce484222325ull;
+        double u[4];
+        surf_draw(s, pid, 0, 0, u);
+        double x[3] = {s->light[0] + u[0] * (s->light[1] - s->light[0]),
+                       s->light[2] + u[1] * (s->light[3] - s->light[2]), 1.0};
+        double nrm[3] = {0.0, 0.0, -1.0};
+        double b1[3], b2[3], d[3];
+        {
+            const double rr = sqrt(u[2]), ph = 2.0 * OR_PI * u[3], ct = sqrt(fmax(0.0, 1.0 - u[2]));
+            or_onb(nrm, b1, b2);
+            for (int k = 0; k < 3; ++k) d[k] = rr * cos(ph) * b1[k] + rr * sin(ph) * b2[k] + ct * nrm[k];
+        }
+        double w = w0;               /* parameter-free part of the weight */
+        double dlog_path[2] = {0.0, 0.0};
+        double fpath = 1.0;          /* Phong factors of the path so far */
+        if (tal) tal[T_INJECTED] += w0;
+        int end = END_NONE;
+        for (int k = 1;; ++k) {
+            double t;
+            const int id = surf_hit(s, x, d, &t, nrm);
+            if (id == -100) {
+                end = END_ESCAPE;
+                if (tal) tal[T_ESCAPED] += w * fpath;
+                break;
+            }
+            for (int a = 0; a < 3; ++a) x[a] += t * d[a];
+            if (tal) tal[T_COLLISIONS] += 1.0;
+            h = fnv_word(h, (uint32_t)(id + 100));
+            const int phong = id == s->phong;
+            /* mirror direction of the incoming propagation direction */
+            const double dn = dot3(d, nrm);
+            const double mir[3] = {d[0] - 2.0 * dn * nrm[0], d[1] - 2.0 * dn * nrm[1], d[2] - 2.0 * dn * nrm[2]};
+            /* local estimate toward the camera */
+            int32_t pixv = -1;
+            {
+                const double to[3] = {cam.C[0] - x[0], cam.C[1] - x[1], cam.C[2] - x[2]};
+                const double r2 = dot3(to, to), r = sqrt(r2);
+                const double wc[3] = {to[0] / r, to[1] / r, to[2] / r};
+                const double cn = dot3(nrm, wc);
+                int col, row;
+                const int64_t pix = cn > 0.0 ? project(&cam, x, &col, &row) : -1;
+                if (pix >= 0 && surf_visible(s, x, wc, r)) {
+                    pixv = (int32_t)pix;
+                    const double cm = dot3(mir, wc);
+                    const double fe = phong ? phong_f(kappa, gamma, cm) : 1.0;
+                    const double om = or_pixel_solid_angle(cam.tx, cam.ty, cam.W, cam.H, col, row);
+                    const double ev = w * fpath * fe / OR_PI * cn / r2 / om;
+                    if (tal) tal[T_IN_VIEW] += 1.0;
+                    if (images) images[pix] += ev * inv_norm;
+                    if (dldi && ev != 0.0) {
+                        double dl[2] = {dlog_path[0], dlog_path[1]};
+                        if (phong) {
+                            double e2[2];
+                            phong_dlog(kappa, gamma, cm, e2);
+                            dl[0] += e2[0];
+                            dl[1] += e2[1];
+                        }
+                        const double A = dldi[pix] * ev * inv_norm;
+                        for (int j = 0; j < 2; ++j) {
+                            grad[j] += A * dl[j];
+                            if (gabs) gabs[j] += fabs(A * dl[j]);
+                        }
+                    }
+                }
+            }
+            h = fnv_word(h, (uint32_t)pixv);
+            surf_draw(s, pid, (uint32_t)k, 0, u);
+            if (k == s->max_orders) {
+                end = END_TRUNC;
+                if (tal) tal[T_TRUNCATED] += w * fpath;
+                break;
+            }
+            if (k >= s->rr_start) {
+                if (u[0] <= s->rr_q) {
+                    if (tal) tal[T_RR_GAIN] += w * fpath * (1.0 / s->rr_q - 1.0);
+                    w /= s->rr_q;
+                } else {
+                    end = END_RR;
+                    if (tal) tal[T_RR_KILLED] += w * fpath;
+                    break;
+                }
+            }
+            /* cosine-weighted direction about the normal */
+            {
+                const double rr = sqrt(u[1]), ph = 2.0 * OR_PI * u[2], ct = sqrt(fmax(0.0, 1.0 - u[1]));
+                or_onb(nrm, b1, b2);
+                for (int a = 0; a < 3; ++a) d[a] = rr * cos(ph) * b1[a] + rr * sin(ph) * b2[a] + ct * nrm[a];
+            }
+            if (phong) {
+                const double c = dot3(mir, d);
+                const double f = phong_f(kappa, gamma, c);
+                if (tal) tal[T_ABSORBED] += w * fpath * (1.0 - f);
+                fpath *= f;
+                double e2[2];
+                phong_dlog(kappa, gamma, c, e2);
+                dlog_path[0] += e2[0];
+                dlog_path[1] += e2[1];
+            }
+        }
+        h = fnv_word(h, (uint32_t)end);
+        if (fp) fp[i] = h;
+    }
+    return 0;
+}

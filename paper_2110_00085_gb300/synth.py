@@ -277,3 +277,52 @@ def small_scene(n: int = 8, n_cams: int = 3, px: int = 8, peak: float = 20.0,
     return Scene(name=f"tiny{n}", n=(n, n, n), voxel=0.02, beta_cloud=beta,
                  beta_air=beta_air, cameras=arc_cameras(n_cams, (n * 0.02,) * 3, px, px),
                  n_paths=n_paths, seed=seed)
+
+
+@dataclasses.dataclass
+class SurfScene:
+    """A closed unit box for the reflectometry workload (Sec. 6): diffuse
+    walls, a square Lambertian emitter in the ceiling (z = 1), diffuse
+    spheres and one sphere (index ``phong``) with the Phong BRDF."""
+    spheres: np.ndarray           # (n, 4): centre, radius
+    phong: int
+    light: tuple                  # emitter x0, x1, y0, y1 on z = 1
+    radiance: float
+    camera: Camera
+    kappa: float = 0.7
+    gamma: float = 50.0
+    max_orders: int = 10
+    rr_start: int = 5
+    rr_q: float = 0.8
+    n_paths: int = 1 << 20
+    seed: int = 1234
+
+    def replace(self, **kw) -> "SurfScene":
+        return dataclasses.replace(self, **kw)
+
+    @property
+    def n_pixels(self) -> int:
+        return self.camera.width * self.camera.height
+
+
+def sphere_box(seed: int = 7, n_small: int = 14, px: int = 60, kappa: float = 0.7, gamma: float = 50.0,
+               n_paths: int = 1 << 20) -> SurfScene:
+    """Seeded stand-in for the reflectometry scene: a Phong sphere (radius
+    0.2) at the centre of the unit box, ``n_small`` diffuse spheres (radius
+    0.04-0.08) placed by rejection (inside the box, apart from each other
+    and from the large sphere, away from the camera), the emitter on the
+    ceiling square [0.35, 0.65]^2 and one camera of ``px`` x ``px`` pixels
+    just inside the front wall, looking at the centre."""
+    rng = np.random.default_rng(seed)
+    sph = [(0.5, 0.5, 0.5, 0.2)]
+    while len(sph) < 1 + n_small:
+        r = float(rng.uniform(0.04, 0.08))
+        c = rng.uniform(r + 0.02, 1.0 - r - 0.02, size=3)
+        if c[1] < 0.25:
+            continue
+        if all(np.linalg.norm(c - np.array(s[:3])) > s[3] + r + 0.02 for s in sph):
+            sph.append((float(c[0]), float(c[1]), float(c[2]), r))
+    cam = Camera(pos=(0.5, 0.02, 0.45), look_at=(0.5, 0.6, 0.5), up=(0.0, 0.0, 1.0),
+                 fov_y=math.radians(70.0), width=px, height=px)
+    return SurfScene(spheres=np.array(sph, dtype=np.float64), phong=0, light=(0.35, 0.65, 0.35, 0.65),
+                     radiance=1.0, camera=cam, kappa=kappa, gamma=gamma, n_paths=n_paths, seed=seed)

@@ -476,3 +476,85 @@ def test_space_carving_keeps_the_cloud_of_single_scatter_images():
     assert cloud.any()
     assert np.all(mask[cloud] == 1)
     assert mask.sum() < 0.5 * mask.size
+
+
+# ------------------------------------------------------------ reflectometry --
+def test_surfaces_energy_balance_and_diffuse_limit():
+    """Closed box (Sec. 6 reflectometry stand-in): injected = escaped +
+    absorbed (Phong factors below 1) + truncated + roulette, to FP64
+    rounding; with kappa = 0 the images do not depend on gamma and the
+    gamma derivative is exactly 0."""
+    ss = synth.sphere_box(n_paths=1 << 14)
+    r = O.surf_render(ss, tallies=True)
+    T = r["tallies"]
+    lhs = T["injected"] + T["rr_gain"]
+    rhs = T["escaped"] + T["absorbed"] + T["truncated"] + T["rr_killed"]
+    assert abs(lhs - rhs) < 1e-10 * lhs and T["absorbed"] > 0
+    a = O.surf_render(ss, kappa=0.0, gamma=5.0)["images"]
+    b = O.surf_render(ss, kappa=0.0, gamma=80.0, dldi=np.ones(ss.n_pixels))
+    assert np.array_equal(a, b["images"])
+    assert b["grad"][1] == 0.0 and b["grad"][0] != 0.0
+
+
+def test_surfaces_gradient_equals_finite_differences():
+    """Paths do not depend on (kappa, gamma), so the gradient of the loss
+    is the exact derivative of the fixed-path estimate: central differences
+    of the FP64 loss in kappa and in gamma."""
+    ss = synth.sphere_box(n_paths=1 << 12)
+    gt = O.surf_render(ss, kappa=0.7, gamma=50.0)["images"]
+    k0, g0 = 0.4, 20.0
+    F = O.surf_render(ss, kappa=k0, gamma=g0)["images"]
+    r = O.surf_render(ss, kappa=k0, gamma=g0, dldi=F - gt, grad_abs=True)
+
+    def loss(k, g):
+        return 0.5 * float(np.sum((O.surf_render(ss, kappa=k, gamma=g)["images"] - gt) ** 2))
+
+    for j, (h, args) in enumerate(((1e-5, lambda e: (k0 + e, g0)), (1e-3, lambda e: (k0, g0 + e)))):
+        fd = (loss(*args(h)) - loss(*args(-h))) / (2 * h)
+        assert abs(fd - r["grad"][j]) <= 1e-6 * r["grad_abs"][j], (j, fd, r["grad"][j])
+
+
+def _view_factor_square(px, py, x0, x1, y0, y1, h=1.0):
+    """View factor from a floor point to the parallel rectangle [x0,x1] x
+    [y0,y1] at height h (Lambertian): sum of four corner rectangles."""
+    def f(a, b):
+        sa, sb = math.sqrt(a * a + h * h), math.sqrt(b * b + h * h)
+        return (a / sa * math.atan(b / sa) + b / sb * math.atan(a / sb)) / (2.0 * math.pi)
+    return f(x1 - px, y1 - py) - f(x0 - px, y1 - py) - f(x1 - px, y0 - py) + f(x0 - px, y0 - py)
+
+
+def test_surfaces_first_order_floor_radiance_closed_form():
+    """No spheres, first order only: the floor's radiance is the emitter's
+    radiance times the view factor to the emitter (diffuse, no absorption),
+    so pixels that see the floor average to the closed form."""
+    ss = synth.sphere_box(n_paths=1 << 21).replace(spheres=np.zeros((0, 4)), phong=-1, max_orders=1)
+    img = O.surf_render(ss)["images"].reshape(ss.camera.height, ss.camera.width)
+    # closed form per pixel: floor points on a fine grid, binned by pixel
+    acc = np.zeros_like(img); cnt = np.zeros_like(img)
+    for xx in np.linspace(0.005, 0.995, 120):
+        for yy in np.linspace(0.005, 0.995, 120):
+            q = O.pixel_coords(_surf_as_scene(ss), 0, (xx, yy, 0.0))
+            if q is None:
+                continue
+            c, rr = int(q[0]), int(q[1])
+            if 0 <= c < ss.camera.width and 0 <= rr < ss.camera.height:
+                acc[rr, c] += ss.radiance * _view_factor_square(xx, yy, *ss.light)
+                cnt[rr, c] += 1
+    # pixels that see only floor: covered by floor points, as their 8 neighbours
+    cov = cnt >= 4
+    seen = cov.copy()
+    for dr in (-1, 0, 1):
+        for dc in (-1, 0, 1):
+            seen &= np.roll(np.roll(cov, dr, 0), dc, 1)
+    seen[0, :] = seen[-1, :] = False
+    seen[:, 0] = seen[:, -1] = False
+    assert seen.sum() > 150
+    want = acc[seen] / cnt[seen]
+    got = img[seen]
+    assert abs(got.mean() - want.mean()) < 0.02 * want.mean(), (got.mean(), want.mean())
+
+
+def _surf_as_scene(ss):
+    """A volume scene with the same single camera, for pixel_coords."""
+    return synth.Scene(name="cam", n=(1, 1, 1), voxel=1.0, beta_cloud=np.zeros((1, 1, 1), np.float32),
+                       cameras=[ss.camera])
