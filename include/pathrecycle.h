@@ -233,6 +233,63 @@ int space_carve(const pt_scene* scene, const double* images, double threshold,
                 uint8_t* mask, void* stream);
 
 /*
+ * Reflectometry (Sec. 6): light paths among surfaces (the surface rendering
+ * equation of Sec. 3) in the closed unit box [0,1]^3 -- diffuse walls, a
+ * square Lambertian emitter of the given radiance in the ceiling z = 1,
+ * diffuse spheres and one sphere (index phong) with the Phong BRDF
+ * f_r = 1 - kappa + kappa (r . w')^gamma (Eq. phong) taken as f_r / pi,
+ * r the mirror of the incoming direction, the cosine clamped at 0.  Paths
+ * start on the emitter (cosine-weighted), make a local estimate toward the
+ * camera at every hit (BRDF times the cosine at the hit, the visibility of
+ * the camera, 1/r^2 and the pixel response 1/Omega) and continue in a
+ * cosine-weighted direction; roulette and the order limit as for volumes.
+ * The path pdf does not depend on (kappa, gamma): stored paths are
+ * re-evaluated under new parameters exactly (Eq. 19).
+ *   surf_scene_create : copies the spheres (host float[n_spheres * 4]:
+ *                  centre, radius) and the camera.  Synchronous.
+ *   surf_store   : traces paths first .. first+n-1 (n < 2^28), seed, epoch
+ *                  (Philox counter as render_forward, scene id 0), keeping
+ *                  per camera event the parameter-free factors and per
+ *                  path the lobe cosines of its Phong vertices; tallies
+ *                  (nullable, accumulated): injected, hits (collisions),
+ *                  camera events (in_view); fingerprints (nullable, n):
+ *                  per path, FNV-1a of (surface, pixel or -1) per hit and
+ *                  the end.
+ *   surf_reweight: images (device float64[W*H], zeroed unless
+ *                  PT_ACCUMULATE) of the stored paths under (kappa, gamma)
+ *                  divided by n_norm; keeps each event's contribution.
+ *   surf_grad    : grad (device float64[2], zeroed unless PT_ACCUMULATE)
+ *                  += d loss / d (kappa, gamma) for dL_dI (device float64
+ *                  [W*H]), from the contributions of the latest
+ *                  surf_reweight, which must have used the same (kappa,
+ *                  gamma).
+ */
+typedef struct {
+    int32_t n_spheres;
+    const float* spheres;        /* host, n_spheres x 4: centre, radius  */
+    int32_t phong;               /* index of the Phong sphere, -1 none   */
+    float light[4];              /* emitter on z = 1: x0, x1, y0, y1     */
+    float radiance;
+    pt_camera camera;
+    int32_t max_orders, rr_start;
+    float rr_q;
+} pt_surf_desc;
+
+typedef struct pt_surf pt_surf;
+typedef struct pt_surf_paths pt_surf_paths;
+int surf_scene_create(const pt_surf_desc* desc, pt_surf** out);
+int surf_scene_free(pt_surf* scene);
+int64_t surf_scene_pixels(const pt_surf* scene);
+int surf_store(const pt_surf* scene, uint64_t first_path, uint64_t n_paths, double n_norm, uint64_t seed,
+               uint32_t epoch, pt_surf_paths** paths, double* tallies, uint64_t* fingerprints, void* stream);
+int surf_reweight(pt_surf_paths* paths, double kappa, double gamma, double* images, uint32_t flags,
+                  void* stream);
+int surf_grad(pt_surf_paths* paths, double kappa, double gamma, const double* dL_dI, double* grad,
+              uint32_t flags, void* stream);
+int surf_paths_events(const pt_surf_paths* paths, uint64_t* n_events);   /* synchronous */
+int surf_paths_free(pt_surf_paths* paths);
+
+/*
  * Batches: many scenes (each with its own grid size, cameras and stored
  * paths) run each pass in one persistent launch.  Resident blocks pull
  * (scene, tile) work items from a device counter (tiles of 128 paths, 128

@@ -109,7 +109,7 @@ def lib():
             L.or_single_scatter_quad.argtypes = [C.POINTER(ORScene), _fp, C.c_int, C.c_int, _dp]
             L.or_camera_frame.argtypes = [C.POINTER(ORScene), C.c_int, _dp]
             L.or_surf_render.argtypes = [C.POINTER(ORSurf), C.c_double, C.c_double, C.c_uint64, C.c_uint64,
-                                         C.c_double, _dp, _dp, _dp, _dp, _dp, _u64p]
+                                         C.c_double, _dp, _dp, _dp, _dp, _dp, _u64p, _dp, _dp]
             L.or_surf_render.restype = C.c_int
             L.or_space_carve.argtypes = [C.POINTER(ORScene), _dp, C.c_double, C.POINTER(C.c_uint8)]
             L.or_pixel_coords.argtypes = [C.POINTER(ORScene), C.c_int, _dp, _dp]
@@ -364,7 +364,10 @@ def pixel_coords(sc, cam: int, x):
 
 
 def _surf(ss, epoch: int = 0, seed=None):
-    sph = np.ascontiguousarray(np.asarray(ss.spheres, dtype=np.float64).reshape(-1))
+    """ctypes scene; the geometry, light and camera are rounded through
+    float32, the precision in which a float32 implementation receives them."""
+    f32 = lambda v: float(np.float32(v))
+    sph = np.ascontiguousarray(np.asarray(ss.spheres, dtype=np.float32).astype(np.float64).reshape(-1))
     st = ORSurf()
     st.n_spheres = len(sph) // 4
     st.phong = int(ss.phong)
@@ -372,24 +375,26 @@ def _surf(ss, epoch: int = 0, seed=None):
     st.rr_start = int(ss.rr_start)
     st.epoch = int(epoch)
     st.seed = int(ss.seed if seed is None else seed)
-    st.rr_q = float(ss.rr_q)
+    st.rr_q = f32(ss.rr_q)
     for i in range(4):
-        st.light[i] = float(ss.light[i])
-    st.radiance = float(ss.radiance)
+        st.light[i] = f32(ss.light[i])
+    st.radiance = f32(ss.radiance)
     st.spheres = sph.ctypes.data_as(C.POINTER(C.c_double))
     c = ss.camera
-    vals = list(c.pos) + list(c.look_at) + list(c.up) + [c.fov_y, c.width, c.height]
+    vals = [f32(v) for v in list(c.pos) + list(c.look_at) + list(c.up) + [c.fov_y]] + [c.width, c.height]
     for i in range(12):
         st.cam[i] = float(vals[i])
     return st, sph
 
 
 def surf_render(ss, kappa=None, gamma=None, first: int = 0, n=None, n_norm=None, dldi=None, grad_abs: bool = False,
-                tallies: bool = False, fingerprints: bool = False, epoch: int = 0, seed=None):
+                tallies: bool = False, fingerprints: bool = False, epoch: int = 0, seed=None,
+                image_cond: bool = False, grad_cond: bool = False):
     """Reflectometry scene ``ss`` (synth.SurfScene): paths [first, first+n)
     evaluated under (kappa, gamma) (default: the scene's).  Returns images
     (W*H), and when asked grad / grad_abs (2: d loss / d kappa, d gamma),
-    tallies (dict) and fingerprints."""
+    tallies (dict), fingerprints, and the float32 budgets image_cond (W*H)
+    and grad_cond (2), measured by perturbed re-sampling as render's."""
     L = lib()
     st, keep = _surf(ss, epoch, seed)
     n = int(ss.n_paths if n is None else n)
@@ -408,8 +413,15 @@ def surf_render(ss, kappa=None, gamma=None, first: int = 0, n=None, n_norm=None,
             out["grad_abs"] = ga
     tal = np.zeros(L.or_tally_count(), dtype=np.float64) if tallies else None
     fp = np.zeros(n, dtype=np.uint64) if fingerprints else None
+    ic = np.zeros(ss.n_pixels) if image_cond else None
+    gc = np.zeros(2) if (grad_cond and dl is not None) else None
+    if ic is not None:
+        out["image_cond"] = ic
+    if gc is not None:
+        out["grad_cond"] = gc
     rc = L.or_surf_render(C.byref(st), kappa, gamma, C.c_uint64(first), C.c_uint64(n), n_norm, _ptr(img, _dp),
-                          _ptr(dl, _dp), _ptr(g, _dp), _ptr(ga, _dp), _ptr(tal, _dp), _ptr(fp, _u64p))
+                          _ptr(dl, _dp), _ptr(g, _dp), _ptr(ga, _dp), _ptr(tal, _dp), _ptr(fp, _u64p),
+                          _ptr(ic, _dp), _ptr(gc, _dp))
     if rc != 0:
         raise RuntimeError(f"or_surf_render failed ({rc})")
     if tal is not None:

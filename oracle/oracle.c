@@ -1195,7 +1195,8 @@ static void phong_dlog(double kappa, double gamma, double c, double out[2])
 /* nearest surface along p + t d (d unit, p inside the box): returns the
  * surface id (spheres 0..n-1, walls -1..-6 for x-, x+, y-, y+, z-, z+) and
  * fills t and the normal facing the ray; no surface (numerically) -> -100 */
-static int surf_hit(const or_surf* s, const double p[3], const double d[3], double* t_out, double n[3])
+static int surf_hit_p(const or_surf* s, const double p[3], const double d[3], double* t_out, double n[3],
+                      double disc_pert)
 {
     double best = INFINITY;
     int id = -100;
@@ -1203,7 +1204,7 @@ static int surf_hit(const or_surf* s, const double p[3], const double d[3], doub
         const double* c = s->spheres + 4 * i;
         const double oc[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
         const double b = dot3(oc, d), cc = dot3(oc, oc) - c[3] * c[3];
-        const double disc = b * b - cc;
+        const double disc = b * b - cc + disc_pert * (b * b + fabs(cc));
         if (disc < 0.0) continue;
         const double t = -b - sqrt(disc);
         if (t > SURF_EPS && t < best) { best = t; id = i; }
@@ -1226,6 +1227,11 @@ static int surf_hit(const or_surf* s, const double p[3], const double d[3], doub
     return id;
 }
 
+static int surf_hit(const or_surf* s, const double p[3], const double d[3], double* t_out, double n[3])
+{
+    return surf_hit_p(s, p, d, t_out, n, 0.0);
+}
+
 /* is the segment x -> x + r w free of spheres? */
 static int surf_visible(const or_surf* s, const double x[3], const double w[3], double r)
 {
@@ -1241,16 +1247,167 @@ static int surf_visible(const or_surf* s, const double x[3], const double w[3], 
     return 1;
 }
 
+
+/* a random unit vector at right angles to n (for the perturbed re-samplings) */
+static void tangent_dir(uint64_t pid, int k, int r, const double n[3], double e[3])
+{
+    pert_dir(pid, k, r, e);
+    const double en = dot3(e, n);
+    for (int a = 0; a < 3; ++a) e[a] -= en * n[a];
+    const double m = sqrt(dot3(e, e));
+    if (m > 0.0)
+        for (int a = 0; a < 3; ++a) e[a] /= m;
+}
+
+/* one path (identical draws to the CUDA path); pert > 0: perturbed
+ * re-sampling r = pert for the float32 budget -- every direction moves by
+ * OR_PERT_ULPS roundoffs, every hit point by as many roundoffs of its
+ * coordinates along its surface, and every sphere's discriminant by as many
+ * roundoffs of its two terms (it is their difference, nearly 0 for a ray
+ * that grazes the sphere, where the hit moves far); events: epix / eval per hit (1 camera),
+ * the path's gradient terms in gpath[2] */
+static uint64_t surf_path(const or_surf* s, const ocam* cam, double kappa, double gamma, uint64_t pid, int pert,
+                          double inv_norm, double* images, const double* dldi, double* grad, double* gabs,
+                          double* tal, int32_t* epix, double* eval, double gpath[2])
+{
+    uint64_t h = 0xcbf29ce484222325ull;
+    double u[4];
+    const double area = (s->light[1] - s->light[0]) * (s->light[3] - s->light[2]);
+    const double w0 = OR_PI * s->radiance * area;
+    surf_draw(s, pid, 0, 0, u);
+    double x[3] = {s->light[0] + u[0] * (s->light[1] - s->light[0]),
+                   s->light[2] + u[1] * (s->light[3] - s->light[2]), 1.0};
+    double nrm[3] = {0.0, 0.0, -1.0};
+    double b1[3], b2[3], d[3];
+    {
+        const double rr = sqrt(u[2]), ph = 2.0 * OR_PI * u[3], ct = sqrt(fmax(0.0, 1.0 - u[2]));
+        or_onb(nrm, b1, b2);
+        for (int k = 0; k < 3; ++k) d[k] = rr * cos(ph) * b1[k] + rr * sin(ph) * b2[k] + ct * nrm[k];
+    }
+    double w = w0;               /* parameter-free part of the weight */
+    double dlog_path[2] = {0.0, 0.0};
+    double fpath = 1.0;          /* Phong factors of the path so far */
+    if (gpath) gpath[0] = gpath[1] = 0.0;
+    if (tal) tal[T_INJECTED] += w0;
+    int end = END_NONE;
+    for (int k = 1;; ++k) {
+        if (pert) {                                  /* direction roundoff */
+            double e[3];
+            pert_dir(pid, 2 * k, pert, e);
+            for (int a = 0; a < 3; ++a) d[a] += OR_PERT_ULPS * OR_U32 * e[a];
+            normalize3(d);
+        }
+        double t, dp = 0.0;
+        if (pert) {                                  /* discriminant roundoff */
+            double e[3];
+            pert_dir(pid, 2 * k + 64, pert, e);
+            dp = OR_PERT_ULPS * OR_U32 * e[0];
+        }
+        const int id = surf_hit_p(s, x, d, &t, nrm, dp);
+        if (id == -100) {
+            end = END_ESCAPE;
+            if (tal) tal[T_ESCAPED] += w * fpath;
+            break;
+        }
+        for (int a = 0; a < 3; ++a) x[a] += t * d[a];
+        if (pert) {                                  /* hit-point roundoff, along the surface */
+            double e[3];
+            tangent_dir(pid, 2 * k + 1, pert, nrm, e);
+            const double m = OR_PERT_ULPS * OR_U32 * (1.0 + sqrt(dot3(x, x)));
+            for (int a = 0; a < 3; ++a) x[a] += m * e[a];
+        }
+        if (tal) tal[T_COLLISIONS] += 1.0;
+        h = fnv_word(h, (uint32_t)(id + 100));
+        const int phong = id == s->phong;
+        /* mirror direction of the incoming propagation direction */
+        const double dn = dot3(d, nrm);
+        const double mir[3] = {d[0] - 2.0 * dn * nrm[0], d[1] - 2.0 * dn * nrm[1], d[2] - 2.0 * dn * nrm[2]};
+        /* local estimate toward the camera */
+        int32_t pixv = -1;
+        {
+            const double to[3] = {cam->C[0] - x[0], cam->C[1] - x[1], cam->C[2] - x[2]};
+            const double r2 = dot3(to, to), r = sqrt(r2);
+            const double wc[3] = {to[0] / r, to[1] / r, to[2] / r};
+            const double cn = dot3(nrm, wc);
+            int col, row;
+            const int64_t pix = cn > 0.0 ? project(cam, x, &col, &row) : -1;
+            if (pix >= 0 && surf_visible(s, x, wc, r)) {
+                pixv = (int32_t)pix;
+                const double cm = dot3(mir, wc);
+                const double fe = phong ? phong_f(kappa, gamma, cm) : 1.0;
+                const double om = or_pixel_solid_angle(cam->tx, cam->ty, cam->W, cam->H, col, row);
+                const double ev = w * fpath * fe / OR_PI * cn / r2 / om;
+                if (tal) tal[T_IN_VIEW] += 1.0;
+                if (images) images[pix] += ev * inv_norm;
+                if (eval) { epix[k - 1] = pixv; eval[k - 1] = ev * inv_norm; }
+                if (dldi && ev != 0.0) {
+                    double dl[2] = {dlog_path[0], dlog_path[1]};
+                    if (phong) {
+                        double e2[2];
+                        phong_dlog(kappa, gamma, cm, e2);
+                        dl[0] += e2[0];
+                        dl[1] += e2[1];
+                    }
+                    const double A = dldi[pix] * ev * inv_norm;
+                    for (int j = 0; j < 2; ++j) {
+                        if (grad) grad[j] += A * dl[j];
+                        if (gabs) gabs[j] += fabs(A * dl[j]);
+                        if (gpath) gpath[j] += A * dl[j];
+                    }
+                }
+            }
+        }
+        h = fnv_word(h, (uint32_t)pixv);
+        surf_draw(s, pid, (uint32_t)k, 0, u);
+        if (k == s->max_orders) {
+            end = END_TRUNC;
+            if (tal) tal[T_TRUNCATED] += w * fpath;
+            break;
+        }
+        if (k >= s->rr_start) {
+            if (u[0] <= s->rr_q) {
+                if (tal) tal[T_RR_GAIN] += w * fpath * (1.0 / s->rr_q - 1.0);
+                w /= s->rr_q;
+            } else {
+                end = END_RR;
+                if (tal) tal[T_RR_KILLED] += w * fpath;
+                break;
+            }
+        }
+        /* cosine-weighted direction about the normal */
+        {
+            const double rr = sqrt(u[1]), ph = 2.0 * OR_PI * u[2], ct = sqrt(fmax(0.0, 1.0 - u[1]));
+            or_onb(nrm, b1, b2);
+            for (int a = 0; a < 3; ++a) d[a] = rr * cos(ph) * b1[a] + rr * sin(ph) * b2[a] + ct * nrm[a];
+        }
+        if (phong) {
+            const double c = dot3(mir, d);
+            const double f = phong_f(kappa, gamma, c);
+            if (tal) tal[T_ABSORBED] += w * fpath * (1.0 - f);
+            fpath *= f;
+            double e2[2];
+            phong_dlog(kappa, gamma, c, e2);
+            dlog_path[0] += e2[0];
+            dlog_path[1] += e2[1];
+        }
+    }
+    h = fnv_word(h, (uint32_t)end);
+    return h;
+}
+
 /*
  * Paths first .. first+n-1 (sampling independent of the BRDF parameters),
  * evaluated under (kappa, gamma): images (W*H, row-major) += contributions /
  * n_norm; with dldi, grad[2] += d loss / d (kappa, gamma) and gabs[2] the sum
  * of the absolute values of its terms; tallies as or_render's; fingerprints
  * (nullable): per path, FNV-1a of (surface id, pixel or -1) per hit and the
- * end.
+ * end.  icond (nullable, W*H) and gcond (nullable, 2, with dldi): float32
+ * budgets measured by perturbed re-sampling as or_render's (test
+ * infrastructure).
  */
 int or_surf_render(const or_surf* s, double kappa, double gamma, uint64_t first, uint64_t n, double n_norm,
-                   double* images, const double* dldi, double* grad, double* gabs, double* tal, uint64_t* fp)
+                   double* images, const double* dldi, double* grad, double* gabs, double* tal, uint64_t* fp,
+                   double* icond, double* gcond)
 {
     or_scene tmp;
     memset(&tmp, 0, sizeof(tmp));
@@ -1259,111 +1416,37 @@ int or_surf_render(const or_surf* s, double kappa, double gamma, uint64_t first,
     ocam cam;
     setup_cams(&tmp, &cam);
     const double inv_norm = 1.0 / n_norm;
-    const double area = (s->light[1] - s->light[0]) * (s->light[3] - s->light[2]);
-    const double w0 = OR_PI * s->radiance * area;
+    const int K = s->max_orders > 0 ? s->max_orders : 1;
+    int32_t e0p[OR_MAXV], e1p[OR_MAXV];
+    double e0v[OR_MAXV], e1v[OR_MAXV], dm[OR_MAXV], g0[2], g1[2];
     for (uint64_t i = 0; i < n; ++i) {
         const uint64_t pid = first + i;
-        uint64_t h = 0xcbf29ce484222325ull;
-        double u[4];
-        surf_draw(s, pid, 0, 0, u);
-        double x[3] = {s->light[0] + u[0] * (s->light[1] - s->light[0]),
-                       s->light[2] + u[1] * (s->light[3] - s->light[2]), 1.0};
-        double nrm[3] = {0.0, 0.0, -1.0};
-        double b1[3], b2[3], d[3];
-        {
-            const double rr = sqrt(u[2]), ph = 2.0 * OR_PI * u[3], ct = sqrt(fmax(0.0, 1.0 - u[2]));
-            or_onb(nrm, b1, b2);
-            for (int k = 0; k < 3; ++k) d[k] = rr * cos(ph) * b1[k] + rr * sin(ph) * b2[k] + ct * nrm[k];
-        }
-        double w = w0;               /* parameter-free part of the weight */
-        double dlog_path[2] = {0.0, 0.0};
-        double fpath = 1.0;          /* Phong factors of the path so far */
-        if (tal) tal[T_INJECTED] += w0;
-        int end = END_NONE;
-        for (int k = 1;; ++k) {
-            double t;
-            const int id = surf_hit(s, x, d, &t, nrm);
-            if (id == -100) {
-                end = END_ESCAPE;
-                if (tal) tal[T_ESCAPED] += w * fpath;
-                break;
-            }
-            for (int a = 0; a < 3; ++a) x[a] += t * d[a];
-            if (tal) tal[T_COLLISIONS] += 1.0;
-            h = fnv_word(h, (uint32_t)(id + 100));
-            const int phong = id == s->phong;
-            /* mirror direction of the incoming propagation direction */
-            const double dn = dot3(d, nrm);
-            const double mir[3] = {d[0] - 2.0 * dn * nrm[0], d[1] - 2.0 * dn * nrm[1], d[2] - 2.0 * dn * nrm[2]};
-            /* local estimate toward the camera */
-            int32_t pixv = -1;
-            {
-                const double to[3] = {cam.C[0] - x[0], cam.C[1] - x[1], cam.C[2] - x[2]};
-                const double r2 = dot3(to, to), r = sqrt(r2);
-                const double wc[3] = {to[0] / r, to[1] / r, to[2] / r};
-                const double cn = dot3(nrm, wc);
-                int col, row;
-                const int64_t pix = cn > 0.0 ? project(&cam, x, &col, &row) : -1;
-                if (pix >= 0 && surf_visible(s, x, wc, r)) {
-                    pixv = (int32_t)pix;
-                    const double cm = dot3(mir, wc);
-                    const double fe = phong ? phong_f(kappa, gamma, cm) : 1.0;
-                    const double om = or_pixel_solid_angle(cam.tx, cam.ty, cam.W, cam.H, col, row);
-                    const double ev = w * fpath * fe / OR_PI * cn / r2 / om;
-                    if (tal) tal[T_IN_VIEW] += 1.0;
-                    if (images) images[pix] += ev * inv_norm;
-                    if (dldi && ev != 0.0) {
-                        double dl[2] = {dlog_path[0], dlog_path[1]};
-                        if (phong) {
-                            double e2[2];
-                            phong_dlog(kappa, gamma, cm, e2);
-                            dl[0] += e2[0];
-                            dl[1] += e2[1];
-                        }
-                        const double A = dldi[pix] * ev * inv_norm;
-                        for (int j = 0; j < 2; ++j) {
-                            grad[j] += A * dl[j];
-                            if (gabs) gabs[j] += fabs(A * dl[j]);
-                        }
-                    }
-                }
-            }
-            h = fnv_word(h, (uint32_t)pixv);
-            surf_draw(s, pid, (uint32_t)k, 0, u);
-            if (k == s->max_orders) {
-                end = END_TRUNC;
-                if (tal) tal[T_TRUNCATED] += w * fpath;
-                break;
-            }
-            if (k >= s->rr_start) {
-                if (u[0] <= s->rr_q) {
-                    if (tal) tal[T_RR_GAIN] += w * fpath * (1.0 / s->rr_q - 1.0);
-                    w /= s->rr_q;
-                } else {
-                    end = END_RR;
-                    if (tal) tal[T_RR_KILLED] += w * fpath;
-                    break;
-                }
-            }
-            /* cosine-weighted direction about the normal */
-            {
-                const double rr = sqrt(u[1]), ph = 2.0 * OR_PI * u[2], ct = sqrt(fmax(0.0, 1.0 - u[1]));
-                or_onb(nrm, b1, b2);
-                for (int a = 0; a < 3; ++a) d[a] = rr * cos(ph) * b1[a] + rr * sin(ph) * b2[a] + ct * nrm[a];
-            }
-            if (phong) {
-                const double c = dot3(mir, d);
-                const double f = phong_f(kappa, gamma, c);
-                if (tal) tal[T_ABSORBED] += w * fpath * (1.0 - f);
-                fpath *= f;
-                double e2[2];
-                phong_dlog(kappa, gamma, c, e2);
-                dlog_path[0] += e2[0];
-                dlog_path[1] += e2[1];
-            }
-        }
-        h = fnv_word(h, (uint32_t)end);
+        const int want = icond || (gcond && dldi);
+        for (int j = 0; j < K; ++j) { e0p[j] = -1; e0v[j] = 0.0; dm[j] = 0.0; }
+        const uint64_t h = surf_path(s, &cam, kappa, gamma, pid, 0, inv_norm, images, dldi, grad, gabs, tal,
+                                     want ? e0p : NULL, want ? e0v : NULL, want ? g0 : NULL);
         if (fp) fp[i] = h;
+        if (!want) continue;
+        double gm[2] = {0.0, 0.0};
+        for (int r = 1; r <= OR_PERT_DRAWS; ++r) {
+            for (int j = 0; j < K; ++j) { e1p[j] = -1; e1v[j] = 0.0; }
+            surf_path(s, &cam, kappa, gamma, pid, r, inv_norm, NULL, dldi, NULL, NULL, NULL, e1p, e1v, g1);
+            for (int j = 0; j < K; ++j) {
+                if (e0p[j] == e1p[j]) {
+                    dm[j] = fmax(dm[j], fabs(e1v[j] - e0v[j]));
+                } else if (icond) {
+                    if (e0p[j] >= 0) icond[e0p[j]] += OR_PERT_SAFETY * fabs(e0v[j]) / OR_PERT_DRAWS;
+                    if (e1p[j] >= 0) icond[e1p[j]] += OR_PERT_SAFETY * fabs(e1v[j]) / OR_PERT_DRAWS;
+                }
+            }
+            if (dldi)
+                for (int j = 0; j < 2; ++j) gm[j] = fmax(gm[j], fabs(g1[j] - g0[j]));
+        }
+        if (icond)
+            for (int j = 0; j < K; ++j)
+                if (e0p[j] >= 0) icond[e0p[j]] += OR_PERT_SAFETY * dm[j];
+        if (gcond && dldi)
+            for (int j = 0; j < 2; ++j) gcond[j] += OR_PERT_SAFETY * gm[j];
     }
     return 0;
 }

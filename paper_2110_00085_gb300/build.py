@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpathrecycle.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["pt_sample.cu", "pt_paths.cu", "pt_events.cu", "pt_batch.cu", "pt_api.cu", "pt_static.cu"]
+SOURCES = ["pt_sample.cu", "pt_paths.cu", "pt_events.cu", "pt_batch.cu", "pt_api.cu", "pt_static.cu",
+           "pt_surf.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -167,6 +167,9 @@ struct pt_scene {
     int64_t n_pixels = 0;
 };
 
+const DevCam* pt::scene_cams(const pt_scene* sc) { return sc->d_cams; }
+const float* pt::scene_omega(const pt_scene* sc) { return sc->d_omega; }
+
 struct pt_paths {
     const pt_scene* scene = nullptr;
     uint64_t n = 0;            // paths of the latest store

@@ -12,6 +12,7 @@ import os
 import threading
 from typing import Optional
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -425,6 +426,129 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             load().batch_free(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------ reflectometry --
+class PtSurfDesc(C.Structure):
+    _fields_ = [("n_spheres", C.c_int32), ("spheres", C.POINTER(C.c_float)), ("phong", C.c_int32),
+                ("light", C.c_float * 4), ("radiance", C.c_float), ("camera", PtCamera),
+                ("max_orders", C.c_int32), ("rr_start", C.c_int32), ("rr_q", C.c_float)]
+
+
+_surf_bound = False
+
+
+def _surf_lib():
+    global _surf_bound
+    L = load()
+    if not _surf_bound:
+        L.surf_scene_create.argtypes = [C.POINTER(PtSurfDesc), C.POINTER(_vp)]
+        L.surf_scene_free.argtypes = [_vp]
+        L.surf_scene_pixels.argtypes = [_vp]
+        L.surf_scene_pixels.restype = C.c_int64
+        L.surf_store.argtypes = [_vp, C.c_uint64, C.c_uint64, C.c_double, C.c_uint64, C.c_uint32, C.POINTER(_vp),
+                                 _vp, _vp, _vp]
+        L.surf_reweight.argtypes = [_vp, C.c_double, C.c_double, _vp, C.c_uint32, _vp]
+        L.surf_grad.argtypes = [_vp, C.c_double, C.c_double, _vp, _vp, C.c_uint32, _vp]
+        L.surf_paths_events.argtypes = [_vp, C.POINTER(C.c_uint64)]
+        L.surf_paths_free.argtypes = [_vp]
+        _surf_bound = True
+    return L
+
+
+class SurfScene:
+    """Device scene of the reflectometry workload (synth.SurfScene)."""
+
+    def __init__(self, ss):
+        L = _surf_lib()
+        self.spec = ss
+        self._sph = np.ascontiguousarray(np.asarray(ss.spheres, dtype=np.float32).reshape(-1))
+        d = PtSurfDesc()
+        d.n_spheres = len(self._sph) // 4
+        d.spheres = self._sph.ctypes.data_as(C.POINTER(C.c_float))
+        d.phong = int(ss.phong)
+        d.light[:] = [float(v) for v in ss.light]
+        d.radiance = float(ss.radiance)
+        c = ss.camera
+        d.camera.pos[:] = [float(v) for v in c.pos]
+        d.camera.look_at[:] = [float(v) for v in c.look_at]
+        d.camera.up[:] = [float(v) for v in c.up]
+        d.camera.fov_y = float(c.fov_y)
+        d.camera.width = int(c.width)
+        d.camera.height = int(c.height)
+        d.max_orders = int(ss.max_orders)
+        d.rr_start = int(ss.rr_start)
+        d.rr_q = float(ss.rr_q)
+        h = _vp()
+        _check(L.surf_scene_create(C.byref(d), C.byref(h)), "surf_scene_create")
+        self._h = h
+        self.n_pixels = int(L.surf_scene_pixels(h))
+
+    def new_images(self) -> torch.Tensor:
+        return torch.zeros(self.n_pixels, dtype=torch.float64, device="cuda")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _surf_lib().surf_scene_free(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SurfPaths:
+    """Stored light paths of a SurfScene, re-evaluated under BRDF parameters."""
+
+    def __init__(self, scene: SurfScene):
+        self.scene = scene
+        self._h = _vp()
+
+    def store(self, n_paths: int, seed: int, first: int = 0, n_norm=None, epoch: int = 0, tallies=None,
+              fingerprints=None, stream=None):
+        n_norm = float(n_paths if n_norm is None else n_norm)
+        rc = _surf_lib().surf_store(self.scene._h, first, n_paths, n_norm, seed, epoch, C.byref(self._h),
+                                    _opt(tallies, torch.float64, "tallies", TALLY_COUNT),
+                                    _opt(fingerprints, torch.int64, "fingerprints", n_paths), _vp(_stream(stream)))
+        _check(rc, "surf_store")
+        return self
+
+    def reweight(self, kappa: float, gamma: float, images=None, accumulate: bool = False, stream=None):
+        if images is None:
+            images = self.scene.new_images()
+        rc = _surf_lib().surf_reweight(self._h, float(kappa), float(gamma),
+                                       _dev(images, torch.float64, "images", self.scene.n_pixels),
+                                       PT_ACCUMULATE if accumulate else 0, _vp(_stream(stream)))
+        _check(rc, "surf_reweight")
+        return images
+
+    def grad(self, kappa: float, gamma: float, dldi, grad=None, accumulate: bool = False, stream=None):
+        if grad is None:
+            grad = torch.zeros(2, dtype=torch.float64, device="cuda")
+        rc = _surf_lib().surf_grad(self._h, float(kappa), float(gamma),
+                                   _dev(dldi, torch.float64, "dL_dI", self.scene.n_pixels),
+                                   _dev(grad, torch.float64, "grad", 2), PT_ACCUMULATE if accumulate else 0,
+                                   _vp(_stream(stream)))
+        _check(rc, "surf_grad")
+        return grad
+
+    def events(self) -> int:
+        n = C.c_uint64(0)
+        _check(_surf_lib().surf_paths_events(self._h, C.byref(n)), "surf_paths_events")
+        return n.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _surf_lib().surf_paths_free(self._h)
             self._h = _vp()
 
     def __del__(self):
