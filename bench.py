@@ -412,6 +412,130 @@ def run_recon(args, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
+
+SURF_TRUTHS = ((0.7, 50.0), (0.5, 30.0))
+SURF_N = 1_800_000
+SURF_LR, SURF_DECAY, SURF_HOLD, SURF_SEEDS = 0.1, 100.0, 50, 3
+
+
+def run_surfaces(args, ws, rank, local):
+    """Reflectometry of Sec. 6: the Phong sphere at the centre of a box with
+    14 diffuse spheres, one camera of 60x60 pixels, N = 1.8e6 light paths,
+    Adam from (kappa, gamma) = (0.3, 20) toward each of the paper's two
+    truths, (0.7, 50) and (0.5, 30), with the paths re-traced every N_r = 30
+    steps and every step (N_r = 1); decorrelated gradient (two halves of
+    the path set), step size 0.1 / (1 + (t-1)/100).  Ground truth: 8N paths
+    of an independent seed (untimed).  Each arm runs args.surf_steps steps
+    for SURF_SEEDS path seeds; the steps are CUDA events apart and the Adam
+    kernel records (kappa, gamma) after each, so the steps and times to
+    eps <= 1% (first reached) and eps <= 2% (held for 50 steps) are read
+    after the run without a host round trip inside it; medians over the
+    seeds."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as G
+    G.build()
+    from paper_2110_00085_gb300 import native as N
+    from paper_2110_00085_gb300 import synth
+    from paper_2110_00085_gb300.driver import SurfReconstruction, surf_error
+
+    torch.cuda.set_device(local)
+    n, S = SURF_N, int(args.surf_steps)
+    ss = synth.sphere_box(n_paths=n)
+    scene = N.SurfScene(ss)
+    try:
+        pr = torch.cuda.get_device_properties(local)
+        gpu_id = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+    except Exception:
+        gpu_id = str(local)
+    clocks = Clocks(gpu_id)
+
+    def reached(e, thr):
+        k = np.nonzero(e <= thr)[0]
+        return int(k[0]) if k.size else None
+
+    def held(e, thr):
+        return next((k for k in range(S - SURF_HOLD + 1) if (e[k:k + SURF_HOLD] <= thr).all()), None)
+
+    def med(xs):
+        xs = [x for x in xs if x is not None]
+        return float(np.median(xs)) if len(xs) * 2 > SURF_SEEDS else None   # a majority of the seeds got there
+
+    runs, launches, total_ms, total_steps, cks = [], 0, 0.0, 0, []
+    for kt, gt_ in SURF_TRUTHS:
+        gt = scene.new_images()
+        for j in range(8):
+            p = N.SurfPaths(scene).store(n, ss.seed + 7919, first=j * n, n_norm=8 * n)
+            p.reweight(kt, gt_, gt, accumulate=j > 0)
+            p.close()
+        arms = {}
+        for n_r in (30, 1):
+            per = []
+            for r in range(SURF_SEEDS):
+                kw = dict(n_r=n_r, lr=SURF_LR, lr_decay=SURF_DECAY, seed=ss.seed + 1000 * r + rank)
+                w = SurfReconstruction(scene, gt, 0.3, 20.0, n, **kw)     # warm-up: the same arm, untimed
+                w.prepare()
+                for _ in range(max(args.warmup, 3)):
+                    w.step(use_graph=True)
+                w.close()
+                rec = SurfReconstruction(scene, gt, 0.3, 20.0, n, trace=S, **kw)
+                rec.prepare()
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(S + 1)]
+                barrier(ws)
+                torch.cuda.synchronize()
+                clocks.start()
+                ev[0].record()
+                for k in range(S):
+                    rec.step(use_graph=True)
+                    ev[k + 1].record()
+                torch.cuda.synchronize()
+                cks.append(clocks.stop())
+                t_ms = np.cumsum([ev[k].elapsed_time(ev[k + 1]) for k in range(S)])
+                tr = rec.trace.cpu().numpy().reshape(S, 2).astype(np.float64)
+                e = surf_error(tr[:, 0], tr[:, 1], kt, gt_)
+                r1, h2 = reached(e, 0.01), held(e, 0.02)
+                per.append({"steps_to_1pct": None if r1 is None else r1 + 1,
+                            "s_to_1pct": None if r1 is None else float(t_ms[r1]) * 1e-3,
+                            "steps_to_2pct_held": None if h2 is None else h2 + 1,
+                            "s_to_2pct_held": None if h2 is None else float(t_ms[h2]) * 1e-3,
+                            "ms_per_step": float(t_ms[-1]) / S, "eps_end": float(e[-1]),
+                            "kappa_end": float(tr[-1, 0]), "gamma_end": float(tr[-1, 1])})
+                launches += rec.launches
+                total_ms += float(t_ms[-1])
+                total_steps += S
+                rec.close()
+            arms[f"n_r={n_r}"] = {
+                "median": {key: med([q[key] for q in per]) for key in
+                           ("steps_to_1pct", "s_to_1pct", "steps_to_2pct_held", "s_to_2pct_held", "ms_per_step",
+                            "eps_end")},
+                "seeds": per}
+        a, b = arms["n_r=30"]["median"], arms["n_r=1"]["median"]
+        speed = {key: (b[key] / a[key]) if a[key] and b[key] else None
+                 for key in ("s_to_1pct", "s_to_2pct_held", "ms_per_step")}
+        runs.append({"truth": {"kappa": kt, "gamma": gt_}, "eps_start": surf_error(0.3, 20.0, kt, gt_),
+                     "arms": arms, "speedup_n_r30_over_n_r1": speed})
+    ms_step = total_ms / total_steps
+    sm = [c["sm_mhz"] for c in cks if c.get("sm_mhz")]
+    ck = {"sm_mhz": float(np.median(sm)) if sm else None,
+          "sm_max_mhz": max((c.get("sm_max_mhz") or 0) for c in cks) or None,
+          "reasons": sorted({x for c in cks for x in c.get("reasons", [])})}
+    out = {"metric": "paths/s through the reflectometry Adam loop (re-evaluated or re-traced), and time to "
+                     "eps <= 1% / 2%, N_r = 30 vs N_r = 1",
+           "value": ws * n / (max_over_ranks(ws, ms_step) * 1e-3), "unit": UNIT, "n_gpus": ws,
+           "steps": total_steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "surfaces: unit box, Phong sphere r=0.2 + 14 diffuse spheres, ceiling emitter, "
+                                  "one camera 60x60, N=1.8e6 light paths, Adam on (kappa, gamma/50) from (0.3, 20), "
+                                  "step 0.1/(1+(t-1)/100), decorrelated gradient, graph-replayed steps, "
+                                  f"{SURF_SEEDS} path seeds per arm",
+                      "l2": "inputs below L2 (the event store, ~40 MB, stays resident: the workload's own size)"},
+           "surfaces": runs, "gpu_launches": launches, "clocks": ck,
+           "note": "eps = mean relative error of (kappa, gamma); the paper reports eps = 1% after 31 s for "
+                   "the (0.7, 50) scene on its own hardware (context, not a target)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def run_native(args, ws, rank, local):
     import numpy as np
     import torch
@@ -593,7 +717,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-calibration", action="store_true", help="skip the matched-gradient-error arm")
-    ap.add_argument("--workload", default="noise128", choices=["noise128", "batch", "recon"])
+    ap.add_argument("--workload", default="noise128", choices=["noise128", "batch", "recon", "surfaces"])
+    ap.add_argument("--surf-steps", type=int, default=800, help="surfaces workload: Adam steps per arm")
     ap.add_argument("--path-scale", type=int, default=0, help="batch workload: lower every 2^k path budget by k")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
@@ -603,6 +728,8 @@ def main():
         run_batch(args, ws, rank, local)
     elif args.workload == "recon":
         run_recon(args, ws, rank, local)
+    elif args.workload == "surfaces":
+        run_surfaces(args, ws, rank, local)
     else:
         run_native(args, ws, rank, local)
     if ws > 1:

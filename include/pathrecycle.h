@@ -263,6 +263,23 @@ int space_carve(const pt_scene* scene, const double* images, double threshold,
  *                  [W*H]), from the contributions of the latest
  *                  surf_reweight, which must have used the same (kappa,
  *                  gamma).
+ *   surf_reweight_dev, surf_grad_dev: the same with (kappa, gamma) read
+ *                  from device memory (theta: float[2]), so that an
+ *                  optimisation loop needs no host round trip and can be
+ *                  captured in a graph.
+ *   surf_adam_step: one Adam step (Sec. 6's modified Adam: moments b1, b2;
+ *                  bias corrections from the step number) on
+ *                  u = (kappa, gamma / gamma_scale) with gradient
+ *                  (grad[0], grad[1] * gamma_scale), step size
+ *                  lr / (1 + (t - 1) / lr_decay) at step t (lr_decay = 0:
+ *                  constant lr), then the projection onto
+ *                  0 <= kappa <= 1, gamma >= 0 of Eq. phong.  theta
+ *                  (device float[2], in/out), m, v (device float[2], the
+ *                  moments of u), grad (device float64[2]), step (device
+ *                  int32, incremented; bias corrections use the new value).
+ *                  trace (nullable device float[2 * trace_cap]) receives
+ *                  (kappa, gamma) after step t at 2 (t-1) while
+ *                  t <= trace_cap.  One thread; asynchronous.
  */
 typedef struct {
     int32_t n_spheres;
@@ -286,6 +303,12 @@ int surf_reweight(pt_surf_paths* paths, double kappa, double gamma, double* imag
                   void* stream);
 int surf_grad(pt_surf_paths* paths, double kappa, double gamma, const double* dL_dI, double* grad,
               uint32_t flags, void* stream);
+int surf_reweight_dev(pt_surf_paths* paths, const float* theta, double* images, uint32_t flags, void* stream);
+int surf_grad_dev(pt_surf_paths* paths, const float* theta, const double* dL_dI, double* grad, uint32_t flags,
+                  void* stream);
+int surf_adam_step(float* theta, float* m, float* v, const double* grad, int32_t* step, float lr,
+                   float lr_decay, float gamma_scale, float b1, float b2, float eps, float* trace,
+                   int32_t trace_cap, void* stream);
 int surf_paths_events(const pt_surf_paths* paths, uint64_t* n_events);   /* synchronous */
 int surf_paths_free(pt_surf_paths* paths);
 

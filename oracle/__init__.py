@@ -344,6 +344,20 @@ def adam_step(beta, m, v, grad, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     return beta, m, v
 
 
+
+def surf_adam_step(theta, m, v, grad, t, lr, gamma_scale, b1=0.9, b2=0.999, eps=1e-8, lr_decay=0.0):
+    """Adam on u = (kappa, gamma / gamma_scale) with gradient
+    (d/dkappa, gamma_scale d/dgamma) and step size lr / (1 + (t-1)/lr_decay)
+    (lr_decay 0: constant), then the projection onto 0 <= kappa <= 1,
+    gamma >= 0 that Eq. phong requires; fp64 numpy.
+    Returns (theta, m, v), m and v the moments of u."""
+    k, gm = np.asarray(theta, dtype=np.float64)
+    g = np.asarray(grad, dtype=np.float64)
+    if lr_decay > 0:
+        lr = lr / (1.0 + (t - 1) / lr_decay)
+    u, m, v = adam_step([k, gm / gamma_scale], m, v, [g[0], g[1] * gamma_scale], t, lr, b1, b2, eps)
+    return np.array([min(u[0], 1.0), u[1] * gamma_scale]), m, v
+
 def space_carve(sc, images, threshold: float) -> np.ndarray:
     """Photo-hull mask (V uint8, x fastest; 1 = kept) of ``images``
     (camera-major, as render_forward's), see or_space_carve."""

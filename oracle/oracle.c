@@ -1217,8 +1217,15 @@ static int surf_hit_p(const or_surf* s, const double p[3], const double d[3], do
     if (id == -100) return id;
     *t_out = best;
     if (id >= 0) {
+        /* unit normal from the centre to the hit point: divided by the distance
+           itself, not the radius, so that a hit point off the sphere by
+           rounding gives a unit normal (with the radius, the error of a
+           non-unit normal grows along chains of sphere hits) */
         const double* c = s->spheres + 4 * id;
-        for (int k = 0; k < 3; ++k) n[k] = (p[k] + best * d[k] - c[k]) / c[3];
+        double q[3];
+        for (int k = 0; k < 3; ++k) q[k] = p[k] + best * d[k] - c[k];
+        const double ql = sqrt(dot3(q, q));
+        for (int k = 0; k < 3; ++k) n[k] = q[k] / ql;
     } else {
         const int a = (-id - 1) / 2;
         for (int k = 0; k < 3; ++k) n[k] = 0.0;

@@ -80,10 +80,13 @@ __device__ int surf_hit(const SurfDev& S, float3 p, float3 d, float& t_out, floa
     if (id == -100) return id;
     t_out = best;
     if (id >= 0) {
+        // normalised by the distance, not the radius: a hit point off the
+        // sphere by rounding still gives a unit normal, so the next direction
+        // stays unit (otherwise the error grows along chains of sphere hits)
         const float4 c = __ldg(S.sph + id);
-        const float ir = 1.0f / c.w;
-        nrm = make_float3((p.x + best * d.x - c.x) * ir, (p.y + best * d.y - c.y) * ir,
-                          (p.z + best * d.z - c.z) * ir);
+        const float qx = p.x + best * d.x - c.x, qy = p.y + best * d.y - c.y, qz = p.z + best * d.z - c.z;
+        const float iq = 1.0f / sqrtf(qx * qx + qy * qy + qz * qz);
+        nrm = make_float3(qx * iq, qy * iq, qz * iq);
     } else {
         const int a = (-id - 1) / 2;
         const float s = ((-id - 1) % 2) ? -1.0f : 1.0f;
@@ -184,8 +187,14 @@ __device__ __forceinline__ float phong_f(float kappa, float gamma, float c) {
     return 1.0f - kappa + kappa * powf(fmaxf(c, 0.0f), gamma);
 }
 
-__global__ void k_surf_reweight(SurfStore P, float kappa, float gamma, double* __restrict__ images,
-                                float* __restrict__ cache) {
+// (kappa, gamma) come from the arguments, or from device memory when theta is
+// given (the optimiser's parameters, read without a host round trip)
+__global__ void k_surf_reweight(SurfStore P, float kappa, float gamma, const float* __restrict__ theta,
+                                double* __restrict__ images, float* __restrict__ cache) {
+    if (theta) {
+        kappa = theta[0];
+        gamma = theta[1];
+    }
     const uint32_t n_ev = min(*P.count, (uint32_t)P.cap);
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_ev; e += gridDim.x * blockDim.x) {
         const uint4 r = P.ev[e];
@@ -207,8 +216,13 @@ __device__ __forceinline__ float2 phong_dlog(float kappa, float gamma, float c) 
 }
 
 __global__ void __launch_bounds__(256) k_surf_grad(SurfStore P, float kappa, float gamma,
+                                                   const float* __restrict__ theta,
                                                    const double* __restrict__ dldi, const float* __restrict__ cache,
                                                    double* __restrict__ grad) {
+    if (theta) {
+        kappa = theta[0];
+        gamma = theta[1];
+    }
     const uint32_t n_ev = min(*P.count, (uint32_t)P.cap);
     double g0 = 0.0, g1 = 0.0;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_ev; e += gridDim.x * blockDim.x) {
@@ -237,6 +251,38 @@ __global__ void __launch_bounds__(256) k_surf_grad(SurfStore P, float kappa, flo
     if ((threadIdx.x & 31) == 0) {
         if (g0 != 0.0) atomicAdd(grad, g0);
         if (g1 != 0.0) atomicAdd(grad + 1, g1);
+    }
+}
+
+// Adam on u = (kappa, gamma / scale) (one step size suits both), then the
+// projection onto 0 <= kappa <= 1, gamma >= 0 of Eq. phong; the step number
+// lives in device memory (t = ++*step), so the whole update, including the
+// step size lr / (1 + (t - 1) / decay) (decay = 0: constant), can be
+// captured in a graph.  trace[2 (t-1) ..] receives (kappa, gamma) after step t.
+__global__ void k_surf_adam(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
+                            const double* __restrict__ g, int32_t* __restrict__ step, float lr, float decay,
+                            float scale, float b1, float b2, float eps, float* __restrict__ trace,
+                            int32_t trace_cap) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int32_t t = ++(*step);
+    if (decay > 0.0f) lr = (float)((double)lr / (1.0 + (double)(t - 1) / (double)decay));
+    const float inv_bc1 = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
+    const float inv_bc2 = (float)(1.0 / (1.0 - pow((double)b2, (double)t)));
+    const float gu[2] = {__double2float_rn(g[0]), __double2float_rn(g[1] * (double)scale)};
+    float u[2] = {theta[0], theta[1] / scale};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float mj = fmaf(b1, m[j], (1.0f - b1) * gu[j]);
+        const float vj = fmaf(b2, v[j], (1.0f - b2) * gu[j] * gu[j]);
+        m[j] = mj;
+        v[j] = vj;
+        u[j] = fmaxf(u[j] - lr * (mj * inv_bc1) / (sqrtf(vj * inv_bc2) + eps), 0.0f);
+    }
+    theta[0] = fminf(u[0], 1.0f);
+    theta[1] = u[1] * scale;
+    if (trace && t <= trace_cap) {
+        trace[2 * (t - 1)] = theta[0];
+        trace[2 * (t - 1) + 1] = theta[1];
     }
 }
 
@@ -398,9 +444,19 @@ int surf_reweight(pt_surf_paths* p, double kappa, double gamma, double* images, 
     if (!(kappa >= 0.0 && kappa <= 1.0 && gamma >= 0.0)) return fail(PT_E_INVALID, "surf_reweight: kappa in [0,1], gamma >= 0");
     cudaStream_t st = (cudaStream_t)stream;
     if (!(flags & PT_ACCUMULATE)) cudaMemsetAsync(images, 0, sizeof(double) * p->scene->n_pixels, st);
-    k_surf_reweight<<<surf_grid(p->st.cap), 256, 0, st>>>(p->st, (float)kappa, (float)gamma, images, p->cache);
+    k_surf_reweight<<<surf_grid(p->st.cap), 256, 0, st>>>(p->st, (float)kappa, (float)gamma, nullptr, images,
+                                                          p->cache);
     p->cache_valid = true;
     return surf_status("surf_reweight");
+}
+
+int surf_reweight_dev(pt_surf_paths* p, const float* theta, double* images, uint32_t flags, void* stream) {
+    if (!p || !p->scene || !theta || !images) return fail(PT_E_INVALID, "surf_reweight_dev: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!(flags & PT_ACCUMULATE)) cudaMemsetAsync(images, 0, sizeof(double) * p->scene->n_pixels, st);
+    k_surf_reweight<<<surf_grid(p->st.cap), 256, 0, st>>>(p->st, 0.0f, 0.0f, theta, images, p->cache);
+    p->cache_valid = true;
+    return surf_status("surf_reweight_dev");
 }
 
 int surf_grad(pt_surf_paths* p, double kappa, double gamma, const double* dldi, double* grad, uint32_t flags,
@@ -409,8 +465,29 @@ int surf_grad(pt_surf_paths* p, double kappa, double gamma, const double* dldi, 
     if (!p->cache_valid) return fail(PT_E_INVALID, "surf_grad: needs a preceding surf_reweight");
     cudaStream_t st = (cudaStream_t)stream;
     if (!(flags & PT_ACCUMULATE)) cudaMemsetAsync(grad, 0, 2 * sizeof(double), st);
-    k_surf_grad<<<surf_grid(p->st.cap), 256, 0, st>>>(p->st, (float)kappa, (float)gamma, dldi, p->cache, grad);
+    k_surf_grad<<<surf_grid(p->st.cap), 256, 0, st>>>(p->st, (float)kappa, (float)gamma, nullptr, dldi, p->cache,
+                                                      grad);
     return surf_status("surf_grad");
+}
+
+int surf_grad_dev(pt_surf_paths* p, const float* theta, const double* dldi, double* grad, uint32_t flags,
+                  void* stream) {
+    if (!p || !p->scene || !theta || !dldi || !grad) return fail(PT_E_INVALID, "surf_grad_dev: null argument");
+    if (!p->cache_valid) return fail(PT_E_INVALID, "surf_grad_dev: needs a preceding surf_reweight");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!(flags & PT_ACCUMULATE)) cudaMemsetAsync(grad, 0, 2 * sizeof(double), st);
+    k_surf_grad<<<surf_grid(p->st.cap), 256, 0, st>>>(p->st, 0.0f, 0.0f, theta, dldi, p->cache, grad);
+    return surf_status("surf_grad_dev");
+}
+
+int surf_adam_step(float* theta, float* m, float* v, const double* grad, int32_t* step, float lr, float lr_decay,
+                   float gamma_scale, float b1, float b2, float eps, float* trace, int32_t trace_cap, void* stream) {
+    if (!theta || !m || !v || !grad || !step) return fail(PT_E_INVALID, "surf_adam_step: null argument");
+    if (!(gamma_scale > 0.0f) || !(lr >= 0.0f) || !(lr_decay >= 0.0f) || trace_cap < 0)
+        return fail(PT_E_INVALID, "surf_adam_step: gamma_scale > 0, lr >= 0, lr_decay >= 0, trace_cap >= 0");
+    k_surf_adam<<<1, 32, 0, (cudaStream_t)stream>>>(theta, m, v, grad, step, lr, lr_decay, gamma_scale, b1, b2, eps,
+                                                    trace, trace ? trace_cap : 0);
+    return surf_status("surf_adam_step");
 }
 
 int surf_paths_events(const pt_surf_paths* p, uint64_t* n_events) {

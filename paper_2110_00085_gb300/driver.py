@@ -450,3 +450,129 @@ class CoarseToFine:
             if not self.step():
                 break
         return self.history
+
+
+class SurfReconstruction:
+    """Recovery of the Phong parameters of the central sphere (Sec. 6,
+    reflectometry) by Adam on the image loss, the stored paths re-evaluated
+    for n_r steps between re-tracings (n_r = 1: a new path set every step).
+
+    (kappa, gamma) live on the device: the re-evaluation, the gradient and
+    the Adam step (on (kappa, gamma / gamma_scale), so one step size suits
+    both, step size lr / (1 + (t - 1) / lr_decay), projected onto
+    0 <= kappa <= 1, gamma >= 0) read and write them there, so a step needs no host round trip and the steps between
+    re-tracings replay one CUDA graph.  The path pdf does not depend on the
+    parameters, so re-evaluated paths add no importance-weight variance;
+    only re-tracing costs.  ``trace`` steps of (kappa, gamma) are recorded
+    on the device.  The parameter error is
+    eps = (|kappa - kappa*| / kappa* + |gamma - gamma*| / gamma*) / 2
+    (a reading: the paper gives no eps for this scene).
+
+    decorrelate: the paths are stored as two halves A and B, and the
+    gradient is dF_A (F_B - y) + dF_B (F_A - y) (twice the gradient, in
+    expectation exactly the gradient of the expected loss).  With one set,
+    the expectation of dF (F - y) adds half the gradient of the image
+    variance, which pulls gamma, whose loss curvature is weak, off the
+    truth."""
+
+    def __init__(self, scene, gt_images: torch.Tensor, kappa0: float, gamma0: float, n_paths: int,
+                 n_r: int = 30, lr: float = 0.05, gamma_scale: float = 50.0, seed: int = 1234,
+                 b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8, trace: int = 0,
+                 decorrelate: bool = True, lr_decay: float = 0.0):
+        self.scene = scene
+        self.gt = gt_images
+        self.scale = float(gamma_scale)
+        self.decorrelate = bool(decorrelate)
+        self.theta = torch.tensor([kappa0, gamma0], dtype=torch.float32, device="cuda")
+        self.m = torch.zeros(2, dtype=torch.float32, device="cuda")
+        self.v = torch.zeros_like(self.m)
+        self.counter = torch.zeros(1, dtype=torch.int32, device="cuda")
+        self.trace = torch.zeros(2 * trace, dtype=torch.float32, device="cuda") if trace > 0 else None
+        self.n_paths, self.n_r, self.lr, self.seed = int(n_paths), int(n_r), float(lr), int(seed)
+        self.lr_decay = float(lr_decay)
+        self.b1, self.b2, self.eps = b1, b2, eps
+        self.paths = N.SurfPaths(scene)
+        self.images = scene.new_images()
+        self.dldi = torch.zeros_like(self.images)
+        self.loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        if self.decorrelate:
+            self.paths_b = N.SurfPaths(scene)
+            self.images_b = scene.new_images()
+            self.dldi_b = torch.zeros_like(self.images)
+            self.loss_b = torch.zeros(1, dtype=torch.float64, device="cuda")
+        self.g = torch.zeros(2, dtype=torch.float64, device="cuda")
+        self.graph = None
+        self.t = 0
+        self.epoch = 0
+        self.launches = 0
+
+    @property
+    def params(self):
+        k, g = self.theta.tolist()
+        return k, g
+
+    def _store(self):
+        n = self.n_paths
+        if self.decorrelate:
+            h = n // 2
+            self.paths.store(h, self.seed, first=0, epoch=self.epoch)
+            self.paths_b.store(n - h, self.seed, first=h, epoch=self.epoch)
+        else:
+            self.paths.store(n, self.seed, epoch=self.epoch)
+
+    def _body(self):
+        self.paths.reweight_dev(self.theta, self.images)
+        N.loss_residual(self.images, self.gt, self.dldi, self.loss)
+        if self.decorrelate:
+            self.paths_b.reweight_dev(self.theta, self.images_b)
+            N.loss_residual(self.images_b, self.gt, self.dldi_b, self.loss_b)
+            self.paths.grad_dev(self.theta, self.dldi_b, self.g)
+            self.paths_b.grad_dev(self.theta, self.dldi, self.g, accumulate=True)
+        else:
+            self.paths.grad_dev(self.theta, self.dldi, self.g)
+        N.surf_adam_step(self.theta, self.m, self.v, self.g, self.counter, self.lr, self.scale, self.b1, self.b2,
+                         self.eps, trace=self.trace, lr_decay=self.lr_decay)
+
+    def prepare(self):
+        """Allocate the stored-path buffers and capture the step graph
+        without taking a step (the first step traces the paths again)."""
+        if self.graph is None:
+            self._store()
+            torch.cuda.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self._body()
+
+    def step(self, use_graph: bool = False):
+        if self.t % self.n_r == 0:
+            self._store()
+            self.epoch += 1
+            self.launches += 2 if self.decorrelate else 1
+        if use_graph:
+            if self.graph is None:
+                # the stored-path buffers keep their addresses across
+                # re-tracings of the same size, so one capture serves the run
+                torch.cuda.synchronize()
+                self.graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(self.graph):
+                    self._body()
+            self.graph.replay()
+        else:
+            self._body()
+        self.launches += 7 if self.decorrelate else 4
+        self.t += 1
+
+    def error(self, kappa_true: float, gamma_true: float) -> float:
+        k, g = self.params
+        return surf_error(k, g, kappa_true, gamma_true)
+
+    def close(self):
+        self.graph = None
+        self.paths.close()
+        if self.decorrelate:
+            self.paths_b.close()
+
+
+def surf_error(kappa, gamma, kappa_true: float, gamma_true: float):
+    """Mean relative error of the Phong parameters (scalars or arrays)."""
+    return 0.5 * (abs(kappa - kappa_true) / kappa_true + abs(gamma - gamma_true) / gamma_true)

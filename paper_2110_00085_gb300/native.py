@@ -457,6 +457,10 @@ def _surf_lib():
                                  _vp, _vp, _vp]
         L.surf_reweight.argtypes = [_vp, C.c_double, C.c_double, _vp, C.c_uint32, _vp]
         L.surf_grad.argtypes = [_vp, C.c_double, C.c_double, _vp, _vp, C.c_uint32, _vp]
+        L.surf_reweight_dev.argtypes = [_vp, _vp, _vp, C.c_uint32, _vp]
+        L.surf_grad_dev.argtypes = [_vp, _vp, _vp, _vp, C.c_uint32, _vp]
+        L.surf_adam_step.argtypes = [_vp, _vp, _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, C.c_float,
+                                     C.c_float, C.c_float, _vp, C.c_int32, _vp]
         L.surf_paths_events.argtypes = [_vp, C.POINTER(C.c_uint64)]
         L.surf_paths_free.argtypes = [_vp]
         _surf_bound = True
@@ -541,6 +545,26 @@ class SurfPaths:
         _check(rc, "surf_grad")
         return grad
 
+    def reweight_dev(self, theta, images=None, accumulate: bool = False, stream=None):
+        """reweight with (kappa, gamma) read from ``theta`` (device float32[2])."""
+        if images is None:
+            images = self.scene.new_images()
+        rc = _surf_lib().surf_reweight_dev(self._h, _dev(theta, torch.float32, "theta", 2),
+                                           _dev(images, torch.float64, "images", self.scene.n_pixels),
+                                           PT_ACCUMULATE if accumulate else 0, _vp(_stream(stream)))
+        _check(rc, "surf_reweight_dev")
+        return images
+
+    def grad_dev(self, theta, dldi, grad=None, accumulate: bool = False, stream=None):
+        if grad is None:
+            grad = torch.zeros(2, dtype=torch.float64, device="cuda")
+        rc = _surf_lib().surf_grad_dev(self._h, _dev(theta, torch.float32, "theta", 2),
+                                       _dev(dldi, torch.float64, "dL_dI", self.scene.n_pixels),
+                                       _dev(grad, torch.float64, "grad", 2), PT_ACCUMULATE if accumulate else 0,
+                                       _vp(_stream(stream)))
+        _check(rc, "surf_grad_dev")
+        return grad
+
     def events(self) -> int:
         n = C.c_uint64(0)
         _check(_surf_lib().surf_paths_events(self._h, C.byref(n)), "surf_paths_events")
@@ -556,3 +580,19 @@ class SurfPaths:
             self.close()
         except Exception:
             pass
+
+
+def surf_adam_step(theta, m, v, grad, step, lr: float, gamma_scale: float, b1: float = 0.9, b2: float = 0.999,
+                   eps: float = 1e-8, trace=None, lr_decay: float = 0.0, stream=None):
+    """Adam on (kappa, gamma / gamma_scale) with the projection of Eq. phong;
+    theta, m, v: device float32[2]; grad: float64[2]; step: int32[1];
+    step size lr / (1 + (t - 1) / lr_decay) (lr_decay 0: constant);
+    trace (optional float32[2 * T]): (kappa, gamma) after each step."""
+    cap = 0 if trace is None else trace.numel() // 2
+    rc = _surf_lib().surf_adam_step(_dev(theta, torch.float32, "theta", 2), _dev(m, torch.float32, "m", 2),
+                                    _dev(v, torch.float32, "v", 2), _dev(grad, torch.float64, "grad", 2),
+                                    _dev(step, torch.int32, "step", 1), float(lr), float(lr_decay),
+                                    float(gamma_scale), float(b1),
+                                    float(b2), float(eps), _opt(trace, torch.float32, "trace", 2 * cap), cap,
+                                    _vp(_stream(stream)))
+    _check(rc, "surf_adam_step")

@@ -68,6 +68,32 @@ def test_surfaces_images_and_gradient_match_oracle(kappa, gamma):
         assert abs(T[k] - ref["tallies"][k]) <= 12 * len(div) + 1
 
 
+
+def test_chains_of_sphere_hits_keep_unit_directions():
+    """Path 2737446 of seed 84 hits five spheres in a row; with the sphere
+    normal divided by the radius instead of the hit point's distance its
+    float32 direction drifted off unit length by a factor growing at every
+    sphere hit, until a vertex landed next to the camera and one event
+    outweighed the whole image (5.9e6 against 2e-5).  The path is
+    ill-conditioned in any arithmetic (five bounces scale a position error by
+    t / r each, so float32 and FP64 take different pixels), but its events
+    now stay of the oracle's size, and over 2^22 paths the image total agrees
+    with the oracle's to 2e-4."""
+    n = 1 << 22
+    ss = synth.sphere_box(n_paths=n)
+    scene = N.SurfScene(ss)
+    seed = ss.seed + 77
+    one = N.SurfPaths(scene).store(1, seed, first=2737446, n_norm=n)
+    img1 = one.reweight(0.7, 50.0).cpu().numpy()
+    r1 = O.surf_render(ss, 0.7, 50.0, first=2737446, n=1, n_norm=n, seed=seed)["images"]
+    assert 0 < r1.max() and img1.max() <= 10 * r1.max(), (img1.max(), r1.max())
+    one.close()
+    paths = N.SurfPaths(scene).store(n, seed)
+    total = float(paths.reweight(0.7, 50.0).sum())
+    ref = float(O.surf_render(ss, 0.7, 50.0, first=0, n=n, n_norm=n, seed=seed)["images"].sum())
+    paths.close()
+    assert abs(total - ref) <= 2e-4 * ref, (total, ref)
+
 def test_surfaces_reevaluation_is_exact():
     """Stored paths re-evaluated under other parameters and back give the
     same images (only the order of the FP64 additions differs)."""
@@ -78,3 +104,84 @@ def test_surfaces_reevaluation_is_exact():
     torch.cuda.synchronize()
     assert paths.events() > 0
     assert torch.allclose(a, b, rtol=1e-12, atol=0)
+
+
+def test_phong_parameters_are_recovered_with_recycling():
+    """From (kappa, gamma) = (0.3, 20), Adam with the decorrelated gradient,
+    the step size decaying as 0.1 / (1 + (t-1)/100) and stored paths
+    (2^20) re-evaluated for 30 steps recovers the true (0.7, 50) of the
+    Phong sphere (ground truth: 4x the paths, independent seed): the mean
+    of the last 100 of 400 steps is within 1% in kappa and 4% in gamma."""
+    from paper_2110_00085_gb300.driver import SurfReconstruction
+    n = 1 << 20
+    ss = synth.sphere_box(n_paths=n)
+    scene = N.SurfScene(ss)
+    gt = scene.new_images()
+    for j in range(4):
+        g = N.SurfPaths(scene).store(n, ss.seed + 77, first=j * n, n_norm=4 * n)
+        g.reweight(0.7, 50.0, gt, accumulate=j > 0)
+        g.close()
+    rec = SurfReconstruction(scene, gt, 0.3, 20.0, n, n_r=30, lr=0.1, lr_decay=100.0, trace=400)
+    for _ in range(400):
+        rec.step(use_graph=True)
+    torch.cuda.synchronize()
+    tr = rec.trace.cpu().numpy().reshape(400, 2)[-100:].mean(axis=0)
+    assert abs(tr[0] - 0.7) < 0.007 and abs(tr[1] - 50.0) < 2.0, tr
+    rec.close()
+
+
+def test_surface_adam_matches_oracle_and_projects():
+    """The device Adam step on (kappa, gamma / scale), step size decaying as
+    lr / (1 + (t-1)/5), against the FP64 oracle over 12 steps of seeded
+    gradients, which drive kappa into the
+    bound 1 and gamma toward 0 (both projections taken); the trace holds
+    (kappa, gamma) after each step."""
+    rng = np.random.default_rng(3)
+    theta = torch.tensor([0.9, 4.0], dtype=torch.float32, device="cuda")
+    m = torch.zeros(2, dtype=torch.float32, device="cuda")
+    v = torch.zeros_like(m)
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    trace = torch.zeros(2 * 8, dtype=torch.float32, device="cuda")
+    rt, rm, rv = np.array([0.9, 4.0]), np.zeros(2), np.zeros(2)
+    hit = [False, False]
+    for t in range(1, 13):
+        g = np.array([-abs(rng.normal()) * 1e3, abs(rng.normal()) * 1e-2])
+        N.surf_adam_step(theta, m, v, t64(g), step, lr=0.05, gamma_scale=50.0, trace=trace, lr_decay=5.0)
+        rt, rm, rv = O.surf_adam_step(rt, rm, rv, g, t, 0.05, 50.0, lr_decay=5.0)
+        got = theta.cpu().numpy().astype(np.float64)
+        assert np.allclose(got, rt, rtol=1e-5, atol=1e-6), (t, got, rt)
+        hit[0] |= rt[0] == 1.0
+        hit[1] |= rt[1] == 0.0
+    assert all(hit)
+    assert int(step.item()) == 12
+    tr = trace.cpu().numpy().reshape(8, 2)
+    assert tr[-1, 0] == 1.0 and np.all(tr[:, 1] >= 0)
+
+
+def test_device_parameters_and_graph_replay_repeat_the_host_calls():
+    """Re-evaluation and gradient with (kappa, gamma) read from device memory
+    equal the host-argument calls (up to the order of the FP64 atomic
+    additions, which varies from run to run), and 40 steps replayed from a
+    CUDA graph give the trace of 40 eager steps."""
+    from paper_2110_00085_gb300.driver import SurfReconstruction
+    ss, scene, paths, fp, tal = _case(1 << 14)
+    theta = torch.tensor([0.45, 17.0], dtype=torch.float32, device="cuda")
+    a = paths.reweight(0.45, 17.0).clone()
+    dl = a - 0.9 * a.mean()
+    ga = paths.grad(0.45, 17.0, dl).clone()
+    b = paths.reweight_dev(theta)
+    gb = paths.grad_dev(theta, dl)
+    assert torch.allclose(a, b, rtol=1e-12, atol=0) and torch.allclose(ga, gb, rtol=1e-12, atol=0)
+    gt = paths.reweight(0.7, 50.0).clone()
+    traces = []
+    for use_graph in (False, True):
+        rec = SurfReconstruction(scene, gt, 0.3, 20.0, 1 << 14, n_r=15, lr=0.05, seed=11, trace=40)
+        for _ in range(40):
+            rec.step(use_graph=use_graph)
+        torch.cuda.synchronize()
+        traces.append(rec.trace.cpu().numpy())
+        rec.close()
+    assert np.allclose(traces[0], traces[1], rtol=1e-5, atol=0)
+    # Adam's first step: lr against the gradient's sign in u (both negative at (0.3, 20))
+    assert np.allclose(traces[0][:2], [0.35, 22.5], rtol=1e-6)
+    assert len(np.unique(traces[0][0::2])) > 10

@@ -558,3 +558,26 @@ def _surf_as_scene(ss):
     """A volume scene with the same single camera, for pixel_coords."""
     return synth.Scene(name="cam", n=(1, 1, 1), voxel=1.0, beta_cloud=np.zeros((1, 1, 1), np.float32),
                        cameras=[ss.camera])
+
+
+def test_surface_adam_first_step_and_projection():
+    """Adam's first step moves each coordinate of u = (kappa, gamma / s) by
+    exactly lr against the sign of its gradient (the bias-corrected moments
+    are g and g^2), i.e. gamma by lr * s; kappa stops at 1 and gamma at 0
+    (the ranges of Eq. phong)."""
+    th, m, v = O.surf_adam_step([0.5, 30.0], np.zeros(2), np.zeros(2), [3.0, -1e-4], 1, 0.05, 50.0, eps=0.0)
+    assert np.allclose(th, [0.45, 32.5], rtol=0, atol=1e-12)
+    th, _, _ = O.surf_adam_step([0.98, 1.0], np.zeros(2), np.zeros(2), [-2.0, 7.0], 1, 0.05, 50.0, eps=0.0)
+    assert th[0] == 1.0 and th[1] == 0.0
+
+
+
+def test_surface_adam_decayed_step_from_zero_moments():
+    """At step t = 3 with zero moments and lr_decay = 2 the step size is lr / 2
+    and the update is lr/2 (1-b1)/(1-b1^3) / sqrt((1-b2)/(1-b2^3)) per unit
+    of u against the gradient's sign (one gradient seen, bias-corrected)."""
+    b1, b2 = 0.9, 0.999
+    d = 0.5 * 0.04 * ((1 - b1) / (1 - b1 ** 3)) / np.sqrt((1 - b2) / (1 - b2 ** 3))
+    th, _, _ = O.surf_adam_step([0.5, 30.0], np.zeros(2), np.zeros(2), [1.0, -1.0], 3, 0.04, 50.0, eps=0.0,
+                                lr_decay=2.0)
+    assert np.allclose(th, [0.5 - d, 30.0 + 50.0 * d], rtol=0, atol=1e-12)
