@@ -22,7 +22,10 @@
  *     with M_t = M_ref it is the plain estimator of Eq. (forward_simulation);
  *   - the loss gradient sum_d (F_d - I_d) dF_d/dbeta_v with the path score
  *     function of scattering tomography (Sec. 4.4 and Appendix C, the
- *     equation closing Sec. C.1), evaluated term by term per event.
+ *     equation closing Sec. C.1), evaluated term by term per event;
+ *   - reflectometry (Sec. 6): light paths among surfaces (the surface
+ *     rendering equation of Sec. 3) with one Phong sphere (Eq. phong),
+ *     local estimates at every hit, and the gradient in (kappa, gamma).
  *
  * Readings where the paper is silent or inconsistent are marked READING.
  * Parity status: every function here is pinned by the CPU test suite
