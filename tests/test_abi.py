@@ -77,3 +77,15 @@ def test_oracle_is_not_imported_by_the_package():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "oracle.c" not in txt, f
+
+
+def test_surface_entry_points_reject_null_arguments_without_a_gpu():
+    from paper_2110_00085_gb300 import native as N
+    L = N._surf_lib()
+    assert L.surf_scene_create(None, None) == 1
+    assert L.surf_store(None, 0, 1, 1.0, 0, 0, None, None, None, None) == 1
+    assert L.surf_reweight(None, 0.5, 10.0, None, 0, None) == 1
+    assert L.surf_reweight_dev(None, None, None, 0, None) == 1
+    assert L.surf_grad_dev(None, None, None, None, 0, None) == 1
+    assert L.surf_adam_step(None, None, None, None, None, 0.1, 0.0, 50.0, 0.9, 0.999, 1e-8, None, 0, None) == 1
+    assert b"null" in L.pt_last_error()
