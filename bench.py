@@ -652,7 +652,7 @@ def run_native(args, ws, rank, local):
     shd_x = T["shadow_cross"]
     # The voxel traversal is bound by the ALU pipe (compares, selects,
     # min/max, integer index updates; the FMA pipe carries the rest).  Its
-    # algorithmic ALU work per voxel crossing (derivation in the design doc):
+    # algorithmic ALU work per voxel crossing, counted step by step:
     # next face = min of three (2), clipped segment length (2), end test (1),
     # axis choice (3), per-axis counter selects (3), index step select and
     # add (3), running t (1), bounds test (1) = 16 lane operations.
