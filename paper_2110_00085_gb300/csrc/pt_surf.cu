@@ -244,13 +244,31 @@ __global__ void __launch_bounds__(256) k_surf_grad(SurfStore P, float kappa, flo
         g0 += a * (double)dl.x;
         g1 += a * (double)dl.y;
     }
+    // both sums go to the same two addresses: reduce over the block first, so
+    // that one FP64 atomic per block and parameter reaches memory
     for (int o = 16; o > 0; o >>= 1) {
         g0 += __shfl_xor_sync(0xffffffffu, g0, o);
         g1 += __shfl_xor_sync(0xffffffffu, g1, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-        if (g0 != 0.0) atomicAdd(grad, g0);
-        if (g1 != 0.0) atomicAdd(grad + 1, g1);
+    __shared__ double part[2][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        part[0][warp] = g0;
+        part[1][warp] = g1;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        g0 = lane < nw ? part[0][lane] : 0.0;
+        g1 = lane < nw ? part[1][lane] : 0.0;
+        for (int o = 4; o > 0; o >>= 1) {
+            g0 += __shfl_xor_sync(0xffffffffu, g0, o);
+            g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+        }
+        if (lane == 0) {
+            if (g0 != 0.0) atomicAdd(grad, g0);
+            if (g1 != 0.0) atomicAdd(grad + 1, g1);
+        }
     }
 }
 
