@@ -465,7 +465,7 @@ def run_surfaces(args, ws, rank, local):
     for kt, gt_ in SURF_TRUTHS:
         gt = scene.new_images()
         for j in range(8):
-            p = N.SurfPaths(scene).store(n, ss.seed + 7919, first=j * n, n_norm=8 * n)
+            p = N.SurfPaths(scene).store(n, ss.seed + 7919, first=j * n, n_norm=8 * n, sort=False)
             p.reweight(kt, gt_, gt, accumulate=j > 0)
             p.close()
         arms = {}

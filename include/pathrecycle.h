@@ -59,6 +59,10 @@ extern "C" {
                                  contributions in the handle; render_grad: use
                                  them instead of re-tracing shadow rays (the
                                  caller guarantees beta_t is unchanged)        */
+#define PT_SORT 4u            /* surf_store: counting-sort the events by pixel,
+                                 so that each re-evaluation merges same-pixel
+                                 terms before its FP64 adds (pays off when the
+                                 paths are re-evaluated more than once)       */
 
 /* tallies: float64[PT_TALLY_COUNT], same meaning as the CPU oracle's */
 enum {
@@ -254,7 +258,9 @@ int space_carve(const pt_scene* scene, const double* images, double threshold,
  *                  (nullable, accumulated): injected, hits (collisions),
  *                  camera events (in_view); fingerprints (nullable, n):
  *                  per path, FNV-1a of (surface, pixel or -1) per hit and
- *                  the end.
+ *                  the end.  flags: PT_SORT orders the kept events by pixel
+ *                  (a counting sort after tracing); results are the same
+ *                  either way up to the order of the FP64 additions.
  *   surf_reweight: images (device float64[W*H], zeroed unless
  *                  PT_ACCUMULATE) of the stored paths under (kappa, gamma)
  *                  divided by n_norm; keeps each event's contribution.
@@ -298,7 +304,8 @@ int surf_scene_create(const pt_surf_desc* desc, pt_surf** out);
 int surf_scene_free(pt_surf* scene);
 int64_t surf_scene_pixels(const pt_surf* scene);
 int surf_store(const pt_surf* scene, uint64_t first_path, uint64_t n_paths, double n_norm, uint64_t seed,
-               uint32_t epoch, pt_surf_paths** paths, double* tallies, uint64_t* fingerprints, void* stream);
+               uint32_t epoch, pt_surf_paths** paths, double* tallies, uint64_t* fingerprints, uint32_t flags,
+               void* stream);
 int surf_reweight(pt_surf_paths* paths, double kappa, double gamma, double* images, uint32_t flags,
                   void* stream);
 int surf_grad(pt_surf_paths* paths, double kappa, double gamma, const double* dL_dI, double* grad,

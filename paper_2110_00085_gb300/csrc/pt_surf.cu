@@ -35,7 +35,11 @@ struct SurfDev {
 };
 
 struct SurfStore {
-    uint4* ev;             // {base bits, lobe cosine bits (or kNoPhong), pixel, path | phong count << 28}
+    uint4* ev;             // {base bits, lobe cosine bits (or kNoPhong), pixel, path | phong count << 28},
+                           // sorted by pixel
+    uint4* raw;            // the same records in the order the tracer wrote them
+    uint32_t* bins;        // per pixel: event count [0, n_pix), then the scatter cursor [n_pix, 2 n_pix)
+    uint32_t n_pix;
     uint32_t* count;       // events written
     float* pc;             // lobe cosines of the Phong continuations, [slot * n + path]
     uint64_t n, cap;
@@ -149,7 +153,7 @@ __global__ void __launch_bounds__(128) k_surf_store(SurfDev S, SurfStore P, uint
                 const float cm = phong ? mir.x * q.dir.x + mir.y * q.dir.y + mir.z * q.dir.z : kNoPhong;
                 const uint32_t pos = atomicAdd(P.count, 1u);
                 if (pos < P.cap)
-                    P.ev[pos] = make_uint4(__float_as_uint(base), __float_as_uint(cm), (uint32_t)q.pix,
+                    P.raw[pos] = make_uint4(__float_as_uint(base), __float_as_uint(cm), (uint32_t)q.pix,
                                            (uint32_t)i | ((uint32_t)m << 28));
             }
         }
@@ -187,24 +191,87 @@ __device__ __forceinline__ float phong_f(float kappa, float gamma, float c) {
     return 1.0f - kappa + kappa * powf(fmaxf(c, 0.0f), gamma);
 }
 
+// Counting sort of the events by pixel, once per store: histogram, one-block
+// exclusive scan, scatter.  (The pixel is in range by construction; the clamp
+// keeps every index inside the bins.)
+__device__ __forceinline__ uint32_t ev_pixel(const SurfStore& P, const uint4& r) { return min(r.z, P.n_pix - 1u); }
+
+__global__ void k_surf_hist(SurfStore P) {
+    const uint32_t n_ev = min(*P.count, (uint32_t)P.cap);
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_ev; e += gridDim.x * blockDim.x)
+        atomicAdd(P.bins + ev_pixel(P, P.raw[e]), 1u);
+}
+
+__global__ void __launch_bounds__(1024) k_surf_scan(SurfStore P) {
+    __shared__ uint32_t part[1024];
+    const uint32_t n = P.n_pix, per = (n + 1023u) / 1024u;
+    const uint32_t lo = min(threadIdx.x * per, n), hi = min(lo + per, n);
+    uint32_t s = 0;
+    for (uint32_t k = lo; k < hi; ++k) s += P.bins[k];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        const uint32_t v = threadIdx.x >= (unsigned)d ? part[threadIdx.x - d] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+    for (uint32_t k = lo; k < hi; ++k) {
+        const uint32_t c = P.bins[k];
+        P.bins[n + k] = run;
+        run += c;
+    }
+}
+
+__global__ void k_surf_scatter(SurfStore P) {
+    const uint32_t n_ev = min(*P.count, (uint32_t)P.cap);
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_ev; e += gridDim.x * blockDim.x) {
+        const uint4 r = P.raw[e];
+        P.ev[atomicAdd(P.bins + P.n_pix + ev_pixel(P, r), 1u)] = r;
+    }
+}
+
 // (kappa, gamma) come from the arguments, or from device memory when theta is
-// given (the optimiser's parameters, read without a host round trip)
+// given (the optimiser's parameters, read without a host round trip).  A warp
+// takes 32 consecutive events (sorted by pixel), sums the contributions of
+// each run of equal pixels in FP64 (a segmented shuffle scan) and sends one
+// red per run.
 __global__ void k_surf_reweight(SurfStore P, float kappa, float gamma, const float* __restrict__ theta,
                                 double* __restrict__ images, float* __restrict__ cache) {
     if (theta) {
         kappa = theta[0];
         gamma = theta[1];
     }
-    const uint32_t n_ev = min(*P.count, (uint32_t)P.cap);
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_ev; e += gridDim.x * blockDim.x) {
-        const uint4 r = P.ev[e];
-        const uint32_t i = r.w & 0x0fffffffu, m = r.w >> 28;
-        float f = __uint_as_float(r.x);
-        for (uint32_t k = 0; k < m; ++k) f *= phong_f(kappa, gamma, P.pc[(uint64_t)k * P.n + i]);
-        const float cm = __uint_as_float(r.y);
-        if (cm > -1.5f) f *= phong_f(kappa, gamma, cm);
-        red_add(images + r.z, f);
-        cache[e] = f;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint64_t n_ev = min(*P.count, (uint32_t)P.cap);
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t c = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c * 32 < n_ev; c += warps) {
+        const uint64_t e = c * 32 + lane;
+        int key = -1 - lane;   // never equal across lanes
+        double sum = 0.0;
+        if (e < n_ev) {
+            const uint4 r = P.ev[e];
+            const uint32_t i = r.w & 0x0fffffffu, m = r.w >> 28;
+            float f = __uint_as_float(r.x);
+            for (uint32_t k = 0; k < m; ++k) f *= phong_f(kappa, gamma, P.pc[(uint64_t)k * P.n + i]);
+            const float cm = __uint_as_float(r.y);
+            if (cm > -1.5f) f *= phong_f(kappa, gamma, cm);
+            cache[e] = f;
+            key = (int)ev_pixel(P, r);
+            sum = (double)f;
+        }
+        const int prev = __shfl_up_sync(full, key, 1);
+        const unsigned heads = __ballot_sync(full, lane == 0 || prev != key);
+        const int start = 31 - __clz(heads & ((2u << lane) - 1u));
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const double o = __shfl_up_sync(full, sum, d);
+            if (lane - d >= start) sum += o;
+        }
+        const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+        if (tail && key >= 0 && sum != 0.0) atomicAdd(images + key, sum);
     }
 }
 
@@ -327,6 +394,14 @@ struct pt_surf_paths {
 namespace {
 unsigned surf_grid(uint64_t n) { return (unsigned)std::min<uint64_t>((n + 255) / 256, 152 * 16); }
 
+void free_store(pt_surf_paths* p) {
+    cudaFree(p->st.ev); cudaFree(p->st.raw); cudaFree(p->st.bins); cudaFree(p->st.pc); cudaFree(p->st.count);
+    cudaFree(p->cache);
+    p->st = SurfStore{};
+    p->cache = nullptr;
+    p->n_cap = 0;
+}
+
 int surf_status(const char* what) {
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PT_OK : fail(PT_E_CUDA, "%s launch: %s", what, cudaGetErrorString(e));
@@ -409,7 +484,7 @@ int surf_scene_free(pt_surf* s) {
 int64_t surf_scene_pixels(const pt_surf* s) { return s ? s->n_pixels : 0; }
 
 int surf_store(const pt_surf* s, uint64_t first, uint64_t n, double n_norm, uint64_t seed, uint32_t epoch,
-               pt_surf_paths** pp, double* tallies, uint64_t* fps, void* stream) {
+               pt_surf_paths** pp, double* tallies, uint64_t* fps, uint32_t flags, void* stream) {
     if (!s || !pp) return fail(PT_E_INVALID, "surf_store: null scene or handle slot");
     if (n == 0 || n >= (1ull << 28)) return fail(PT_E_INVALID, "surf_store: n_paths must be in 1..2^28-1");
     if (!(n_norm > 0.0)) return fail(PT_E_INVALID, "surf_store: n_norm must be > 0");
@@ -425,35 +500,43 @@ int surf_store(const pt_surf* s, uint64_t first, uint64_t n, double n_norm, uint
     p->scene = s;
     if (p->n_cap < n) {
         if (!created) cudaStreamSynchronize(st);
-        cudaFree(p->st.ev); cudaFree(p->st.pc); cudaFree(p->st.count); cudaFree(p->cache);
-        p->st = SurfStore{};
-        p->cache = nullptr;
-        p->n_cap = 0;
+        free_store(p);
         const uint64_t cap = n * (uint64_t)s->dev.max_orders;
         if (cudaMalloc(&p->st.ev, sizeof(uint4) * cap) != cudaSuccess ||
+            cudaMalloc(&p->st.raw, sizeof(uint4) * cap) != cudaSuccess ||
+            cudaMalloc(&p->st.bins, sizeof(uint32_t) * 2 * (uint64_t)s->n_pixels) != cudaSuccess ||
             cudaMalloc(&p->st.pc, sizeof(float) * n * 15) != cudaSuccess ||
             cudaMalloc(&p->st.count, sizeof(uint32_t)) != cudaSuccess ||
             cudaMalloc(&p->cache, sizeof(float) * cap) != cudaSuccess) {
             cudaGetLastError();
-            cudaFree(p->st.ev); cudaFree(p->st.pc); cudaFree(p->st.count); cudaFree(p->cache);
-            p->st = SurfStore{};
-            p->cache = nullptr;
+            free_store(p);
             if (created) delete p;
             return fail(PT_E_OOM, "surf_store: no device memory for %llu paths", (unsigned long long)n);
         }
         p->n_cap = n;
         p->st.cap = cap;
+        p->st.n_pix = (uint32_t)s->n_pixels;
     }
     *pp = p;
     p->st.n = n;
     p->cache_valid = false;
+    const bool sort = (flags & PT_SORT) != 0;
     cudaMemsetAsync(p->st.count, 0, sizeof(uint32_t), st);
+    if (sort) cudaMemsetAsync(p->st.bins, 0, sizeof(uint32_t) * p->st.n_pix, st);
+    // the tracer writes the kept buffer directly unless a sort follows
+    SurfStore w = p->st;
+    if (!sort) w.raw = w.ev;
     Rng rng{};
     rng.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     rng.epoch = epoch;
     rng.scene = 0;
-    k_surf_store<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(s->dev, p->st, first, (float)(1.0 / n_norm), rng,
+    k_surf_store<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(s->dev, w, first, (float)(1.0 / n_norm), rng,
                                                              tallies, fps);
+    if (sort) {
+        k_surf_hist<<<surf_grid(p->st.cap), 256, 0, st>>>(p->st);
+        k_surf_scan<<<1, 1024, 0, st>>>(p->st);
+        k_surf_scatter<<<surf_grid(p->st.cap), 256, 0, st>>>(p->st);
+    }
     return surf_status("surf_store");
 }
 
@@ -520,7 +603,7 @@ int surf_paths_events(const pt_surf_paths* p, uint64_t* n_events) {
 int surf_paths_free(pt_surf_paths* p) {
     if (!p) return PT_OK;
     cudaDeviceSynchronize();
-    cudaFree(p->st.ev); cudaFree(p->st.pc); cudaFree(p->st.count); cudaFree(p->cache);
+    free_store(p);
     delete p;
     return PT_OK;
 }

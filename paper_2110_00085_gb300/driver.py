@@ -513,12 +513,13 @@ class SurfReconstruction:
 
     def _store(self):
         n = self.n_paths
+        sort = self.n_r > 1        # sorting events by pixel pays off only for re-used paths
         if self.decorrelate:
             h = n // 2
-            self.paths.store(h, self.seed, first=0, epoch=self.epoch)
-            self.paths_b.store(n - h, self.seed, first=h, epoch=self.epoch)
+            self.paths.store(h, self.seed, first=0, epoch=self.epoch, sort=sort)
+            self.paths_b.store(n - h, self.seed, first=h, epoch=self.epoch, sort=sort)
         else:
-            self.paths.store(n, self.seed, epoch=self.epoch)
+            self.paths.store(n, self.seed, epoch=self.epoch, sort=sort)
 
     def _body(self):
         self.paths.reweight_dev(self.theta, self.images)
@@ -547,7 +548,7 @@ class SurfReconstruction:
         if self.t % self.n_r == 0:
             self._store()
             self.epoch += 1
-            self.launches += 2 if self.decorrelate else 1
+            self.launches += (4 if self.n_r > 1 else 1) * (2 if self.decorrelate else 1)   # trace (+ sort)
         if use_graph:
             if self.graph is None:
                 # the stored-path buffers keep their addresses across

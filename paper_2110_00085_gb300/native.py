@@ -19,6 +19,7 @@ from . import build as _build
 
 PT_ACCUMULATE = 1
 PT_CACHE = 2
+PT_SORT = 4
 TALLY_NAMES = ["injected", "missed", "escaped", "absorbed", "truncated", "rr_killed",
                "rr_gain", "collisions", "entered", "seg_cross", "shadow_cross", "in_view"]
 TALLY_COUNT = len(TALLY_NAMES)
@@ -454,7 +455,7 @@ def _surf_lib():
         L.surf_scene_pixels.argtypes = [_vp]
         L.surf_scene_pixels.restype = C.c_int64
         L.surf_store.argtypes = [_vp, C.c_uint64, C.c_uint64, C.c_double, C.c_uint64, C.c_uint32, C.POINTER(_vp),
-                                 _vp, _vp, _vp]
+                                 _vp, _vp, C.c_uint32, _vp]
         L.surf_reweight.argtypes = [_vp, C.c_double, C.c_double, _vp, C.c_uint32, _vp]
         L.surf_grad.argtypes = [_vp, C.c_double, C.c_double, _vp, _vp, C.c_uint32, _vp]
         L.surf_reweight_dev.argtypes = [_vp, _vp, _vp, C.c_uint32, _vp]
@@ -518,11 +519,14 @@ class SurfPaths:
         self._h = _vp()
 
     def store(self, n_paths: int, seed: int, first: int = 0, n_norm=None, epoch: int = 0, tallies=None,
-              fingerprints=None, stream=None):
+              fingerprints=None, sort: bool = True, stream=None):
+        """Trace light paths [first, first + n_paths); ``sort`` orders the kept
+        events by pixel (worth it when the paths are re-evaluated repeatedly)."""
         n_norm = float(n_paths if n_norm is None else n_norm)
         rc = _surf_lib().surf_store(self.scene._h, first, n_paths, n_norm, seed, epoch, C.byref(self._h),
                                     _opt(tallies, torch.float64, "tallies", TALLY_COUNT),
-                                    _opt(fingerprints, torch.int64, "fingerprints", n_paths), _vp(_stream(stream)))
+                                    _opt(fingerprints, torch.int64, "fingerprints", n_paths),
+                                    PT_SORT if sort else 0, _vp(_stream(stream)))
         _check(rc, "surf_store")
         return self
 

@@ -83,7 +83,7 @@ def test_surface_entry_points_reject_null_arguments_without_a_gpu():
     from paper_2110_00085_gb300 import native as N
     L = N._surf_lib()
     assert L.surf_scene_create(None, None) == 1
-    assert L.surf_store(None, 0, 1, 1.0, 0, 0, None, None, None, None) == 1
+    assert L.surf_store(None, 0, 1, 1.0, 0, 0, None, None, None, 0, None) == 1
     assert L.surf_reweight(None, 0.5, 10.0, None, 0, None) == 1
     assert L.surf_reweight_dev(None, None, None, 0, None) == 1
     assert L.surf_grad_dev(None, None, None, None, 0, None) == 1

@@ -96,7 +96,9 @@ def test_chains_of_sphere_hits_keep_unit_directions():
 
 def test_surfaces_reevaluation_is_exact():
     """Stored paths re-evaluated under other parameters and back give the
-    same images (only the order of the FP64 additions differs)."""
+    same images, and a store with its events sorted by pixel gives the same
+    images and gradient as an unsorted one (only the order of the FP64
+    additions differs)."""
     ss, scene, paths, fp, tal = _case(1 << 14)
     a = paths.reweight(0.7, 50.0).clone()
     paths.reweight(0.2, 5.0)
@@ -104,6 +106,15 @@ def test_surfaces_reevaluation_is_exact():
     torch.cuda.synchronize()
     assert paths.events() > 0
     assert torch.allclose(a, b, rtol=1e-12, atol=0)
+    u = N.SurfPaths(scene).store(ss.n_paths, ss.seed, sort=False)
+    assert u.events() == paths.events()
+    c = u.reweight(0.7, 50.0)
+    dl = a - 0.9 * a.mean()
+    g1, g2 = paths.grad(0.7, 50.0, dl), u.grad(0.7, 50.0, dl)
+    torch.cuda.synchronize()
+    assert torch.allclose(a, c, rtol=1e-12, atol=1e-300)
+    assert torch.allclose(g1, g2, rtol=1e-9, atol=0)
+    u.close()
 
 
 def test_phong_parameters_are_recovered_with_recycling():
