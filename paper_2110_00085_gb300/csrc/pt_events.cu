@@ -120,7 +120,9 @@ __global__ void __launch_bounds__(128) k_path_grad(DevScene S, SortedPaths P, Ev
 }
 
 template <bool CACHE>
-__global__ void __launch_bounds__(128) k_event_forward(DevScene S, SortedPaths P, Events E,
+// 16 resident blocks per SM (32 registers, a few spilled bytes): the extra warps
+// hide the beta gathers' latency (97.9 -> 94.9 ms at 2^24 paths, 15 cameras)
+__global__ void __launch_bounds__(128, 16) k_event_forward(DevScene S, SortedPaths P, Events E,
                                                        const float* __restrict__ beta_t,
                                                        const float* __restrict__ beta_ref,
                                                        double* __restrict__ images, float* __restrict__ cache) {
