@@ -395,8 +395,15 @@ int render_forward_static(const pt_scene_desc* desc, const float* beta_cloud,
                           uint32_t flags, void* stream);
 
 /* Synchronises the stream and reports (then clears) kernel-side invariant
- * violations recorded in the scene. */
+ * violations recorded in the scene: PT_E_DEVICE_ASSERT, the text naming the
+ * bits (1 voxel index out of range, 2 traversal longer than the grid allows,
+ * 4 stored record with an invalid voxel). */
 int pt_check(const pt_scene* scene, void* stream);
+
+/* Test hook for the reporting path: ORs `bits` (1, 2, 4 as above) into the
+ * scene's device error word on the stream, as a kernel that detected the
+ * violation would, without running any kernel. */
+int pt_inject_error(pt_scene* scene, int bits, void* stream);
 
 const char* pt_last_error(void);
 const char* pt_version(void);

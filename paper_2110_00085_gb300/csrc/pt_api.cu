@@ -858,4 +858,16 @@ int pt_check(const pt_scene* sc, void* stream) {
     return PT_OK;
 }
 
+int pt_inject_error(pt_scene* sc, int bits, void* stream) {
+    if (!sc) return fail(PT_E_INVALID, "pt_inject_error: null scene");
+    if (bits <= 0 || bits > 7) return fail(PT_E_INVALID, "pt_inject_error: bits must be in 1..7");
+    int h = 0;
+    PT_CUDA(cudaMemcpyAsync(&h, sc->d_err, sizeof(int), cudaMemcpyDeviceToHost, S_(stream)));
+    PT_CUDA(cudaStreamSynchronize(S_(stream)));
+    h |= bits;
+    PT_CUDA(cudaMemcpyAsync(sc->d_err, &h, sizeof(int), cudaMemcpyHostToDevice, S_(stream)));
+    PT_CUDA(cudaStreamSynchronize(S_(stream)));
+    return PT_OK;
+}
+
 }  // extern "C"

@@ -84,6 +84,7 @@ def load():
                                 C.c_float, _vp]
         L.loss_residual.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
         L.space_carve.argtypes = [_vp, _vp, C.c_double, _vp, _vp]
+        L.pt_inject_error.argtypes = [_vp, C.c_int, _vp]
         L.adam_step_counted.argtypes = [_vp, _vp, _vp, _vp, _vp, C.c_int64, _vp, _vp, C.c_float, C.c_float, C.c_float,
                                         C.c_float, _vp]
         L.pt_check.argtypes = [_vp, _vp]
@@ -190,6 +191,10 @@ class Scene:
 
     def check(self, stream=None):
         _check(load().pt_check(self._h, _vp(_stream(stream))), "pt_check")
+
+    def inject_error(self, bits: int, stream=None):
+        """Test hook: record invariant-violation bits as a kernel would."""
+        _check(load().pt_inject_error(self._h, int(bits), _vp(_stream(stream))), "pt_inject_error")
 
     def space_carve(self, images: torch.Tensor, threshold: float, mask: Optional[torch.Tensor] = None,
                     stream=None) -> torch.Tensor:

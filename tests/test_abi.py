@@ -44,6 +44,8 @@ def test_null_arguments_are_rejected_without_a_gpu():
     assert L.paths_reweight(None, None, None, 0, None) == 1
     assert L.render_grad(None, None, None, None, 0, None) == 1
     assert L.adam_step(None, None, None, None, None, 0, 0, 0.0, 0.0, 0.0, 0.0, None) == 1
+    assert L.pt_inject_error(None, 1, None) == 1
+    assert L.pt_check(None, None) == 1
 
 
 def test_scene_descriptor_validation_runs_on_host():

@@ -219,3 +219,21 @@ def test_loss_residual_and_adam_match_reference():
         rb, rm, rv = O.adam_step(rb, rm, rv, g * t, t, lr=0.1)
     assert np.allclose(tb.cpu().numpy(), rb, rtol=1e-5, atol=1e-5)
     assert (tb.cpu().numpy() >= 0).all()
+
+
+def test_device_error_word_is_reported_once_and_cleared():
+    """The reporting path of kernel-side invariant checks: bits recorded in
+    the scene's error word (here by the host hook, as a kernel would) make
+    the next check raise with their meaning and are cleared by it."""
+    sc = synth.config(1, n_paths=1 << 10)
+    scene = N.Scene(sc)
+    scene.check()
+    scene.inject_error(2)
+    with pytest.raises(RuntimeError, match="0x2"):
+        scene.check()
+    scene.check()
+    scene.inject_error(1)
+    scene.inject_error(4)
+    with pytest.raises(RuntimeError, match="0x5"):
+        scene.check()
+    scene.check()
