@@ -156,6 +156,9 @@ int render_forward(const pt_scene* scene, const float* beta_cloud,
  * contribution cache are sized from the actual record and event counts
  * (1/8 headroom), which paths_store reads after its counting sort: the call
  * synchronises the stream once, and growing a buffer synchronises again.
+ * Before tracing, beta_cloud is checked (one more synchronisation): a grid
+ * with NaN, infinite or negative voxels returns PT_E_INVALID, traces
+ * nothing and leaves the handle without paths.
  * n_paths < 2^32 per handle; larger path sets are stored as several handles
  * over ranges of path ids (first_path) sharing n_norm.
  */

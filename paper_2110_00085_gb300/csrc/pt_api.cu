@@ -114,6 +114,16 @@ __global__ void k_adam(float* __restrict__ beta, float* __restrict__ m, float* _
     }
 }
 
+// voxels of an extinction grid that are NaN, infinite or negative
+__global__ void k_check_beta(const float* __restrict__ beta, int64_t n, uint32_t* __restrict__ bad) {
+    uint32_t c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float b = beta[i];
+        if (!(b >= 0.0f) || isinf(b)) ++c;
+    }
+    if (c) atomicAdd(bad, c);
+}
+
 // step counter on the device: t = ++(*step); bias corrections 1/(1 - b^t)
 __global__ void k_adam_count(int32_t* step, float b1, float b2, float* inv_bc) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -182,6 +192,7 @@ struct pt_paths {
     uint4* sa = nullptr;       // sorted records (stream A)
     float4* sb = nullptr;      // sorted records (stream B)
     Buckets* bk = nullptr;
+    uint32_t* bad = nullptr;   // invalid extinction voxels found by the store's check
     Events ev{};               // ev.cap = events the buffers hold
     float* cache = nullptr;
     uint64_t cache_cap = 0;    // floats
@@ -220,6 +231,8 @@ cudaMemPool_t store_pool() {
 
 void free_paths_buffers(pt_paths* p) {
     cudaFree(p->beta_ref); cudaFree(p->dbeta); cudaFree(p->sa); cudaFree(p->sb); cudaFree(p->bk); cudaFree(p->cache);
+    cudaFree(p->bad);
+    p->bad = nullptr;
     cudaFree(p->ev.a); cudaFree(p->ev.b); cudaFree(p->ev.of_rec); cudaFree(p->ev.val); cudaFree(p->ev.hist);
     cudaFree(p->ev.cursor); cudaFree(p->ev.partial);
     p->beta_ref = p->dbeta = nullptr; p->sa = nullptr; p->sb = nullptr;
@@ -419,6 +432,7 @@ int64_t pt_scene_pixels(const pt_scene* sc) { return sc ? sc->n_pixels : -1; }
 
 int render_forward(const pt_scene* sc, const float* beta, uint64_t first, uint64_t n, double n_norm, uint64_t seed,
                    uint32_t epoch, double* images, uint32_t flags, double* tallies, uint64_t* fps, void* stream) {
+    NvtxRange nvtx_range("render_forward");
     if (!sc || !beta || !images) return fail(PT_E_INVALID, "render_forward: null scene, grid or images");
     if (!(n_norm > 0.0)) return fail(PT_E_INVALID, "render_forward: n_norm must be > 0");
     if (n >= ((uint64_t)1 << 40)) return fail(PT_E_INVALID, "render_forward: n_paths too large");
@@ -432,6 +446,7 @@ int render_forward(const pt_scene* sc, const float* beta, uint64_t first, uint64
 int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t n, double n_norm, uint64_t seed,
                 uint32_t epoch, pt_paths** pp, double* images_ref, uint32_t flags, double* tallies, uint64_t* fps,
                 void* stream) {
+    NvtxRange nvtx_range("paths_store");
     if (!sc || !beta || !pp) return fail(PT_E_INVALID, "paths_store: null scene, grid or handle slot");
     if (!(n_norm > 0.0)) return fail(PT_E_INVALID, "paths_store: n_norm must be > 0");
     if (n == 0 || n >= ((uint64_t)1 << 32)) return fail(PT_E_INVALID, "paths_store: n_paths must be in 1..2^32-1");
@@ -469,6 +484,7 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
         if ((rc = dev_alloc(&p->beta_ref, (uint64_t)p->V, &by, "beta_ref")) ||
             (rc = dev_alloc(&p->dbeta, (uint64_t)p->V, &by, "dbeta")) ||
             (rc = dev_alloc(&p->bk, 1, &by, "buckets")) ||
+            (rc = dev_alloc(&p->bad, 1, &by, "extinction check")) ||
             (rc = dev_alloc(&E.hist, E.n_bins, &by, "event bins")) ||
             (rc = dev_alloc(&E.cursor, E.n_bins, &by, "event bin cursors")) ||
             (rc = dev_alloc(&E.partial, 3 * 4096, &by, "scan partials"))) {
@@ -483,6 +499,21 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
     p->inv_norm = (float)(1.0 / n_norm);
     p->cache_valid = false;
     *pp = p;
+
+    // no path kernel runs on an extinction grid with NaN, infinite or negative
+    // voxels: count them first (one synchronisation; the store has another)
+    {
+        uint32_t bad = 0;
+        PT_CUDA(cudaMemsetAsync(p->bad, 0, sizeof(uint32_t), st));
+        k_check_beta<<<grid_for(p->V, 256), 256, 0, st>>>(beta, p->V, p->bad);
+        if ((rc = launch_status("paths_store check"))) return rc;
+        PT_CUDA(cudaMemcpyAsync(&bad, p->bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        PT_CUDA(cudaStreamSynchronize(st));
+        if (bad) {
+            p->n = 0;
+            return fail(PT_E_INVALID, "paths_store: beta has %u voxels that are NaN, infinite or negative", bad);
+        }
+    }
 
     // The sampled records (slot-major, every path's maximum slots) live only
     // until the sort: stream-ordered allocations, returned to the pool after
@@ -566,6 +597,7 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
 }
 
 int paths_reweight(pt_paths* p, const float* beta_t, double* images, uint32_t flags, void* stream) {
+    NvtxRange nvtx_range("paths_reweight");
     if (!p || !p->scene || !beta_t || !images) return fail(PT_E_INVALID, "paths_reweight: null argument");
     if (p->n == 0) return fail(PT_E_INVALID, "paths_reweight: handle holds no paths");
     cudaStream_t st = S_(stream);
@@ -592,6 +624,7 @@ int paths_reweight(pt_paths* p, const float* beta_t, double* images, uint32_t fl
 }
 
 int render_grad(pt_paths* p, const float* beta_t, const double* dldi, double* grad, uint32_t flags, void* stream) {
+    NvtxRange nvtx_range("render_grad");
     if (!p || !p->scene || !beta_t || !dldi || !grad) return fail(PT_E_INVALID, "render_grad: null argument");
     if (p->n == 0) return fail(PT_E_INVALID, "render_grad: handle holds no paths");
     if ((flags & PT_CACHE) && !p->cache_valid)
@@ -659,6 +692,7 @@ int loss_residual(const double* images, const double* gt, int64_t n, double* dld
 }
 
 int space_carve(const pt_scene* sc, const double* images, double threshold, uint8_t* mask, void* stream) {
+    NvtxRange nvtx_range("space_carve");
     if (!sc || !images || !mask) return fail(PT_E_INVALID, "space_carve: null argument");
     cudaStream_t st = S_(stream);
     k_space_carve<<<grid_for(sc->ds.V, 256), 256, 0, st>>>(sc->ds, images, threshold, mask);
@@ -790,6 +824,7 @@ int batch_bind(pt_batch* b, const float* const* beta_t, double* const* images, c
 }
 
 int batch_reweight(pt_batch* b, uint32_t flags, void* stream) {
+    NvtxRange nvtx_range("batch_reweight");
     if (!b || !b->bound) return fail(PT_E_INVALID, "batch_reweight: batch not bound");
     cudaStream_t st = S_(stream);
     const int n = (int)b->paths.size();
@@ -812,6 +847,7 @@ int batch_reweight(pt_batch* b, uint32_t flags, void* stream) {
 }
 
 int batch_grad(pt_batch* b, uint32_t flags, void* stream) {
+    NvtxRange nvtx_range("batch_grad");
     if (!b || !b->bound) return fail(PT_E_INVALID, "batch_grad: batch not bound");
     if (!(flags & PT_CACHE)) return fail(PT_E_INVALID, "batch_grad: the batched gradient reads the cache (PT_CACHE)");
     const int n = (int)b->paths.size();

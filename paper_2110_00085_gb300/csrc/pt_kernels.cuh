@@ -1,12 +1,22 @@
 // pt_kernels.cuh -- kernel launch interfaces shared between the kernel
 // translation units and the C-ABI translation unit.
 #pragma once
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "pt_device.cuh"
 
 namespace pt {
+
+// NVTX range over one library call (the pass names profilers show); header
+// only, and a no-op unless a tool is attached
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // unsorted vertex records written by the sampling kernel: slot k of path i
 // at k * stride + i; cnt[i] = number of collisions B of path i

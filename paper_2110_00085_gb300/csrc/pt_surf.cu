@@ -485,6 +485,7 @@ int64_t surf_scene_pixels(const pt_surf* s) { return s ? s->n_pixels : 0; }
 
 int surf_store(const pt_surf* s, uint64_t first, uint64_t n, double n_norm, uint64_t seed, uint32_t epoch,
                pt_surf_paths** pp, double* tallies, uint64_t* fps, uint32_t flags, void* stream) {
+    NvtxRange nvtx_range("surf_store");
     if (!s || !pp) return fail(PT_E_INVALID, "surf_store: null scene or handle slot");
     if (n == 0 || n >= (1ull << 28)) return fail(PT_E_INVALID, "surf_store: n_paths must be in 1..2^28-1");
     if (!(n_norm > 0.0)) return fail(PT_E_INVALID, "surf_store: n_norm must be > 0");
@@ -541,6 +542,7 @@ int surf_store(const pt_surf* s, uint64_t first, uint64_t n, double n_norm, uint
 }
 
 int surf_reweight(pt_surf_paths* p, double kappa, double gamma, double* images, uint32_t flags, void* stream) {
+    NvtxRange nvtx_range("surf_reweight");
     if (!p || !p->scene || !images) return fail(PT_E_INVALID, "surf_reweight: null argument");
     if (!(kappa >= 0.0 && kappa <= 1.0 && gamma >= 0.0)) return fail(PT_E_INVALID, "surf_reweight: kappa in [0,1], gamma >= 0");
     cudaStream_t st = (cudaStream_t)stream;
@@ -552,6 +554,7 @@ int surf_reweight(pt_surf_paths* p, double kappa, double gamma, double* images, 
 }
 
 int surf_reweight_dev(pt_surf_paths* p, const float* theta, double* images, uint32_t flags, void* stream) {
+    NvtxRange nvtx_range("surf_reweight_dev");
     if (!p || !p->scene || !theta || !images) return fail(PT_E_INVALID, "surf_reweight_dev: null argument");
     cudaStream_t st = (cudaStream_t)stream;
     if (!(flags & PT_ACCUMULATE)) cudaMemsetAsync(images, 0, sizeof(double) * p->scene->n_pixels, st);
@@ -562,6 +565,7 @@ int surf_reweight_dev(pt_surf_paths* p, const float* theta, double* images, uint
 
 int surf_grad(pt_surf_paths* p, double kappa, double gamma, const double* dldi, double* grad, uint32_t flags,
               void* stream) {
+    NvtxRange nvtx_range("surf_grad");
     if (!p || !p->scene || !dldi || !grad) return fail(PT_E_INVALID, "surf_grad: null argument");
     if (!p->cache_valid) return fail(PT_E_INVALID, "surf_grad: needs a preceding surf_reweight");
     cudaStream_t st = (cudaStream_t)stream;
@@ -573,6 +577,7 @@ int surf_grad(pt_surf_paths* p, double kappa, double gamma, const double* dldi, 
 
 int surf_grad_dev(pt_surf_paths* p, const float* theta, const double* dldi, double* grad, uint32_t flags,
                   void* stream) {
+    NvtxRange nvtx_range("surf_grad_dev");
     if (!p || !p->scene || !theta || !dldi || !grad) return fail(PT_E_INVALID, "surf_grad_dev: null argument");
     if (!p->cache_valid) return fail(PT_E_INVALID, "surf_grad_dev: needs a preceding surf_reweight");
     cudaStream_t st = (cudaStream_t)stream;

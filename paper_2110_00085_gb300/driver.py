@@ -133,6 +133,7 @@ class Reconstruction:
         self.loss = torch.zeros(1, dtype=torch.float64, device=self.beta.device)
         self.t = 0
         self.epoch = 0
+        self._need_store = False
         self.launches = 0
         self.mask = None     # optional uint8 voxel mask: voxels with 0 are not optimised
 
@@ -158,7 +159,8 @@ class Reconstruction:
             e.record()
             return e
 
-        if self.t % self.n_r == 0:
+        if self.t % self.n_r == 0 or self._need_store:
+            self._need_store = False
             a = ev() if timers is not None else None
             self.resample()
             if timers is not None:
@@ -204,6 +206,24 @@ class Reconstruction:
         self.v.copy_(snap["v"])
         self.t = snap["t"]
         self.epoch = snap["epoch"]
+
+    def save(self, path: str):
+        """Checkpoint to a file: the snapshot plus the settings that define the
+        path sets (path budget, N_r, seed, estimator)."""
+        snap = {k: (v.cpu() if torch.is_tensor(v) else v) for k, v in self.snapshot().items()}
+        snap.update(n_paths=self.n_paths, n_r=self.n_r, seed=self.seed, decorrelate=self.decorrelate)
+        torch.save(snap, path)
+
+    def load(self, path: str):
+        """Resume from save(): exact from a resample boundary (t mod N_r == 0,
+        the same paths are drawn again); elsewhere the next step draws paths
+        at the loaded extinction, as its stored paths are not in the file."""
+        snap = torch.load(path, map_location="cpu")
+        for k in ("n_paths", "n_r", "seed", "decorrelate"):
+            if snap[k] != getattr(self, k):
+                raise ValueError(f"checkpoint {k} = {snap[k]} differs from this run's {getattr(self, k)}")
+        self.restore(snap)
+        self._need_store = self.t % self.n_r != 0
 
     def close(self):
         self.paths.close()

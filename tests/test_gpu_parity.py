@@ -237,3 +237,45 @@ def test_device_error_word_is_reported_once_and_cleared():
     with pytest.raises(RuntimeError, match="0x5"):
         scene.check()
     scene.check()
+
+
+def test_store_rejects_invalid_extinction_before_tracing():
+    """A grid with a NaN, an infinite or a negative voxel is refused with a
+    status naming the count (no path kernel runs on it); the handle holds no
+    paths afterwards and a valid store on it works."""
+    sc = synth.config(1, n_paths=1 << 10)
+    scene = N.Scene(sc)
+    good = torch.from_numpy(sc.beta_cloud.reshape(-1).astype(np.float32)).cuda()
+    for bad_value in (float("nan"), float("inf"), -1.0):
+        b = good.clone()
+        b[[5, 77]] = bad_value
+        P = N.Paths(scene)
+        with pytest.raises(RuntimeError, match="2 voxels"):
+            P.store(b, 1 << 10, 1)
+        with pytest.raises(RuntimeError, match="no paths"):
+            P.reweight(good)
+        P.store(good, 1 << 10, 1)
+        assert float(P.reweight(good).sum()) > 0
+        P.close()
+    scene.check()
+
+
+def test_repeated_passes_agree_to_summation_order():
+    """Determinism: the same recycled forward and gradient run twice on the
+    same stored paths agree to FP64 summation-order noise (the atomics'
+    order is the only freedom), with and without the contribution cache."""
+    sc = synth.config(1, n_paths=1 << 14)
+    scene = N.Scene(sc)
+    bt = torch.from_numpy(sc.beta_cloud.reshape(-1).astype(np.float32)).cuda()
+    P = N.Paths(scene).store(bt, 1 << 14, 3)
+    b1 = bt * 1.05
+    for cache in (True, False):
+        i1 = P.reweight(b1, cache=cache).clone()
+        dl = i1 - 0.9 * i1.mean()
+        g1 = P.grad(b1, dl, cache=cache).clone()
+        i2 = P.reweight(b1, cache=cache)
+        g2 = P.grad(b1, dl, cache=cache)
+        torch.cuda.synchronize()
+        assert torch.allclose(i1, i2, rtol=1e-12, atol=0)
+        assert float((g1 - g2).abs().sum()) <= 1e-9 * float(g1.abs().sum())
+    P.close()

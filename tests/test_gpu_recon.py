@@ -150,3 +150,33 @@ def test_reconstruction_checkpoint_resume_repeats_steps():
     assert torch.allclose(rec.beta, a, rtol=1e-5, atol=1e-6) and abs(float(rec.loss) - la) <= 1e-9 * abs(la)
     assert not torch.equal(snap["beta"], a)
     rec.close()
+
+
+def test_reconstruction_resumes_from_a_file_checkpoint(tmp_path):
+    """save() at a resample boundary and load() into a new Reconstruction of
+    the same settings (no stored paths yet) repeat the same Adam steps; a
+    checkpoint of other settings is refused."""
+    from paper_2110_00085_gb300.driver import Reconstruction
+    sc = synth.config(1, n_paths=1 << 14)
+    scene = N.Scene(sc)
+    bt = torch.from_numpy(sc.beta_cloud.reshape(-1).astype(np.float32)).cuda()
+    gt = scene.render_forward(bt, 1 << 15, 999)
+    rec = Reconstruction(scene, gt, bt * 0.8, 1 << 14, n_r=3, lr=0.1, seed=5, decorrelate=True)
+    for _ in range(3):
+        rec.step()
+    f = str(tmp_path / "ckpt.pt")
+    rec.save(f)
+    for _ in range(4):
+        rec.step()
+    torch.cuda.synchronize()
+    a = rec.beta.clone()
+    rec.close()
+    other = Reconstruction(scene, gt, bt * 0.5, 1 << 14, n_r=3, lr=0.1, seed=5, decorrelate=True)
+    other.load(f)
+    for _ in range(4):
+        other.step()
+    torch.cuda.synchronize()
+    assert torch.allclose(other.beta, a, rtol=1e-5, atol=1e-6)
+    other.close()
+    with pytest.raises(ValueError, match="seed"):
+        Reconstruction(scene, gt, bt, 1 << 14, n_r=3, lr=0.1, seed=6, decorrelate=True).load(f)
