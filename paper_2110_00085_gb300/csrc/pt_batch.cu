@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_group(const __grid_const
 // 54 -> 9); the delta and path-gradient passes are left alone
 template <int PASS>
 constexpr int cap_blocks() {
-    return PASS == kPassWeights ? 9 : PASS == kPassForward ? 10 : PASS == kPassGrad ? 9 : 1;
+    return PASS == kPassWeights ? 9 : PASS == kPassForward ? 16 : PASS == kPassGrad ? 9 : 1;
 }
 
 template <int PASS, bool CACHE>
