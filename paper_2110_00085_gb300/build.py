@@ -35,6 +35,19 @@ def _deps():
     return files
 
 
+def source_stamp() -> str:
+    """SHA-1 (16 hex digits) of the library's sources and header: identifies
+    the build whose kernels a cached tuning choice was timed on."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in sorted(_deps()):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(f, "rb") as fh:
+                h.update(os.path.basename(f).encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False

@@ -27,9 +27,12 @@ def _cache_path() -> str:
 
 
 def batch_key(scenes, n_paths) -> str:
+    """GPU name, library build (a choice timed on other kernels is not
+    reused) and batch shape."""
+    from . import build as _build
     sig = [(tuple(int(k) for k in sc.spec.n), len(sc.spec.cameras), int(n)) for sc, n in zip(scenes, n_paths)]
     name = torch.cuda.get_device_name()
-    return name + ":" + hashlib.sha1(repr(sig).encode()).hexdigest()[:16]
+    return name + ":" + _build.source_stamp() + ":" + hashlib.sha1(repr(sig).encode()).hexdigest()[:16]
 
 
 def shapes(batch, blocks=(2, 4, 6, 8)):
