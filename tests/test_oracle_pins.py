@@ -581,3 +581,28 @@ def test_surface_adam_decayed_step_from_zero_moments():
     th, _, _ = O.surf_adam_step([0.5, 30.0], np.zeros(2), np.zeros(2), [1.0, -1.0], 3, 0.04, 50.0, eps=0.0,
                                 lr_decay=2.0)
     assert np.allclose(th, [0.5 - d, 30.0 + 50.0 * d], rtol=0, atol=1e-12)
+
+
+def test_phong_factor_is_a_power_of_the_lobe_cosine():
+    """At kappa = 1 a path's Phong factor is the product of c_k^gamma over its
+    Phong vertices (Eq. phong, c clamped at 0), so each event's contribution
+    over its diffuse value (kappa = 0) is r(gamma) = P^gamma for one P per
+    event: r(2) = r(1)^2, r(3) = r(1)^3 and r(2.5) = r(1)^2.5 (real only for
+    r(1) >= 0, which the clamp guarantees).  A wrong exponent or a missing
+    clamp breaks these identities."""
+    ss = synth.sphere_box(n_paths=1 << 10)
+    checked = 0
+    for pid in range(0, 1 << 10):
+        base = O.surf_render(ss, 0.0, 1.0, first=pid, n=1, n_norm=1)["images"]
+        nz = np.nonzero(base)[0]
+        if len(nz) != 1:          # one in-view event: its pixel holds exactly its contribution
+            continue
+        r = [O.surf_render(ss, 1.0, g, first=pid, n=1, n_norm=1)["images"][nz[0]] / base[nz[0]]
+             for g in (1.0, 2.0, 3.0, 2.5)]
+        if r[0] == 1.0:           # no Phong vertex on this event's path
+            continue
+        assert abs(r[1] - r[0] ** 2) <= 1e-12 + 1e-9 * r[0] ** 2, (pid, r)
+        assert abs(r[2] - r[0] ** 3) <= 1e-12 + 1e-9 * r[0] ** 3, (pid, r)
+        assert r[0] >= 0 and abs(r[3] - r[0] ** 2.5) <= 1e-12 + 1e-9 * r[0] ** 2.5, (pid, r)
+        checked += 1
+    assert checked >= 20
