@@ -572,7 +572,9 @@ class SurfReconstruction:
         if use_graph:
             if self.graph is None:
                 # the stored-path buffers keep their addresses across
-                # re-tracings of the same size, so one capture serves the run
+                # re-tracings of the same size (this driver's n_paths is
+                # fixed), so one capture serves the run; a store that grew a
+                # handle would need a new capture
                 torch.cuda.synchronize()
                 self.graph = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(self.graph):
