@@ -606,3 +606,17 @@ def test_phong_factor_is_a_power_of_the_lobe_cosine():
         assert r[0] >= 0 and abs(r[3] - r[0] ** 2.5) <= 1e-12 + 1e-9 * r[0] ** 2.5, (pid, r)
         checked += 1
     assert checked >= 20
+
+
+def test_surface_budgets_leave_the_estimate_unchanged():
+    """Measuring the float32 budgets of the surface paths (perturbed
+    re-sampling) changes neither the images nor the gradient; the budgets
+    are non-negative and not all zero."""
+    ss = synth.sphere_box(n_paths=1 << 11)
+    a = O.surf_render(ss, 0.5, 20.0)
+    dl = a["images"] - 0.9 * a["images"].mean()
+    b = O.surf_render(ss, 0.5, 20.0, dldi=dl, image_cond=True, grad_cond=True)
+    c = O.surf_render(ss, 0.5, 20.0, dldi=dl)
+    assert np.array_equal(a["images"], b["images"]) and np.array_equal(b["grad"], c["grad"])
+    assert np.all(b["image_cond"] >= 0) and b["image_cond"].max() > 0
+    assert np.all(b["grad_cond"] >= 0) and b["grad_cond"].max() > 0
