@@ -91,3 +91,18 @@ def test_surface_entry_points_reject_null_arguments_without_a_gpu():
     assert L.surf_grad_dev(None, None, None, None, 0, None) == 1
     assert L.surf_adam_step(None, None, None, None, None, 0.1, 0.0, 50.0, 0.9, 0.999, 1e-8, None, 0, None) == 1
     assert b"null" in L.pt_last_error()
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/pathrecycle.h is a C header: it compiles as C11 with warnings as
+    errors (no C++ or CUDA types in the boundary)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "t.c"
+    src.write_text('#include "pathrecycle.h"\nint main(void) { pt_scene* s = 0; (void)s; return PT_OK; }\n')
+    r = subprocess.run([cc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), "-c",
+                        str(src), "-o", str(tmp_path / "t.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
