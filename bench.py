@@ -267,10 +267,12 @@ def run_batch(args, ws, rank, local):
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "batch16: 16 blob/noise clouds, sides {32..128}, 5-21 cams 64x64, "
-                                  "2^20-2^23 paths each, N_r=10, batched launches per pass, CUDA graph per step",
+                                  f"2^{20 - args.path_scale}-2^{23 - args.path_scale} paths each, N_r=10, "
+                                  "batched launches per pass, CUDA graph per step",
                       "paths_per_step": total, "launch_shape": {"reg_cap": best[0], "blocks_per_sm": best[1]},
                       "tuning_ms": tim,
-                      "l2": "stored paths of every scene exceed L2"},
+                      "l2": ("stored paths of every scene exceed L2" if args.path_scale == 0 else
+                             "smaller path budgets: part of the stored paths may stay in L2 between passes")},
            "arms_ms_per_step": {k: [r[0] for r in v] for k, v in res.items()},
            "gpu_launches": launches, "clocks": ck}
     if rank == 0:
