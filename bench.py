@@ -279,6 +279,82 @@ def run_batch(args, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
+PROBES = (  # (name, kind, element bytes, buffer elements, iterations per thread, rate unit)
+    ("gather_f32_l2", 0, 4, 1 << 21, 1 << 14, "gathers/s"),        # 8 MB float32 grid (a 128^3 extinction grid)
+    ("red_f64_random_l2", 1, 8, 1 << 21, 1 << 12, "reds/s"),       # 16 MB float64 grid (a 128^3 gradient)
+    ("red_f64_warp_l2", 2, 8, 1 << 21, 1 << 12, "reds/s"),         # 32 consecutive doubles per warp
+    ("red_f64_same_l2", 3, 8, 1 << 21, 1 << 10, "reds/s"),         # one address per warp
+    ("red_f32_random_l2", 4, 4, 1 << 22, 1 << 12, "reds/s"),       # 16 MB float32 grid
+    ("red_f64_random_hbm", 1, 8, 1 << 27, 1 << 12, "reds/s"),      # 1 GB float64 grid (beyond L2)
+)
+
+
+def measure_peaks(dev, reps: int = 10, warmup: int = 3):
+    """Memory rates the recycled passes are bounded by, measured with the
+    library's probes (include/pt_probes.h) on this device: random 4-byte
+    gathers and FP64/FP32 reductions resolved in L2, and a streaming copy
+    through HBM.  Each probe is launched warmup + reps times with a full
+    grid (SMs x 8 blocks of 256 threads); the best CUDA-event time counts
+    (the probes are timed alone, so their burst rate is the denominator)."""
+    import torch
+    from paper_2110_00085_gb300 import native as N
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = sms * 8
+    out = {"sms": sms, "blocks": blocks, "threads_per_block": 256}
+
+    def best_ms(fn):
+        for _ in range(warmup):
+            fn()
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts), statistics.median(ts)
+
+    for name, kind, esz, n, iters, unit in PROBES:
+        buf = torch.zeros(n * esz // 4, dtype=torch.float32, device=dev)
+        sink = torch.zeros(blocks * 256, dtype=torch.float32, device=dev) if kind == 0 else None
+        ms, med = best_ms(lambda: N.probe(kind, buf, iters, blocks, sink=sink))
+        ops = blocks * 256 * iters
+        out[name] = {"rate": ops / (ms * 1e-3), "unit": unit, "bytes_per_op": esz,
+                     "gbs": ops * esz / (ms * 1e-3) / 1e9, "ms_best": ms, "ms_median": med,
+                     "buffer_mb": n * esz / 2 ** 20}
+        del buf, sink
+    n16 = 1 << 28   # 4 GiB each way
+    src = torch.empty(n16 * 4, dtype=torch.float32, device=dev).fill_(1.0)
+    dst = torch.empty_like(src)
+    ms, med = best_ms(lambda: N.probe(5, dst, 0, blocks, src=src))
+    out["copy_hbm"] = {"gbs": 2 * n16 * 16 / (ms * 1e-3) / 1e9, "unit": "GB/s (read + write)",
+                       "ms_best": ms, "ms_median": med, "buffer_mb": n16 * 16 / 2 ** 20}
+    del src, dst
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_peaks(args, ws, rank, local):
+    """The probes alone: one JSON line with the measured L2 and HBM rates."""
+    import torch
+    import __graft_entry__ as G
+    G.build()
+    torch.cuda.set_device(local)
+    pr = torch.cuda.get_device_properties(local)
+    try:
+        gpu_id = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+    except Exception:
+        gpu_id = str(local)
+    clocks = Clocks(gpu_id)
+    clocks.start()
+    pk = measure_peaks(torch.device("cuda", local), reps=max(args.steps, 3), warmup=max(args.warmup, 3))
+    ck = clocks.stop()
+    if rank == 0:
+        print(json.dumps({"probes": pk, "gpu": pr.name, "clocks": ck}), flush=True)
+
+
 def kernel_source_hash() -> str:
     """SHA-1 (16 hex digits) of the event kernels' code: their sources with
     comments and blank space removed, so that only a change of code counts."""
@@ -728,7 +804,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-calibration", action="store_true", help="skip the matched-gradient-error arm")
-    ap.add_argument("--workload", default="noise128", choices=["noise128", "batch", "recon", "surfaces"])
+    ap.add_argument("--workload", default="noise128", choices=["noise128", "batch", "recon", "surfaces", "peaks"])
     ap.add_argument("--surf-steps", type=int, default=800, help="surfaces workload: Adam steps per arm")
     ap.add_argument("--path-scale", type=int, default=0, help="batch workload: lower every 2^k path budget by k")
     args = ap.parse_args()
@@ -741,6 +817,8 @@ def main():
         run_recon(args, ws, rank, local)
     elif args.workload == "surfaces":
         run_surfaces(args, ws, rank, local)
+    elif args.workload == "peaks":
+        run_peaks(args, ws, rank, local)
     else:
         run_native(args, ws, rank, local)
     if ws > 1:

@@ -8,6 +8,7 @@ imports nothing from the package either.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -25,17 +26,24 @@ T_NAMES = ["injected", "missed", "escaped", "absorbed", "truncated", "rr_killed"
            "rr_gain", "collisions", "entered", "seg_cross", "shadow_cross", "in_view"]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_liboracle.so`` (gcc, OpenMP)."""
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+def build(force: bool = False, plant: str = "") -> str:
+    """Compile the oracle into ``oracle/_liboracle.so`` (gcc, OpenMP).
+
+    ``plant`` (tests only) names one of the OR_PLANT_* mistakes of
+    oracle.c; that copy is built into ``oracle/_liboracle_<plant>.so`` and
+    the real oracle is left alone."""
+    path = _LIB_PATH if not plant else os.path.join(_HERE, f"_liboracle_{plant.lower()}.so")
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
            "-std=c11", "-o", tmp, _SRC, "-lm"]
+    if plant:
+        cmd.insert(1, f"-DOR_PLANT_{plant.upper()}")
     subprocess.check_call(cmd)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
 class ORScene(C.Structure):
@@ -79,44 +87,64 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = C.CDLL(_LIB_PATH)
-            L.or_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
-            L.or_fnv1a_words.argtypes = [_u32p, C.c_int]
-            L.or_fnv1a_words.restype = C.c_uint64
-            L.or_phase_hg.argtypes = [C.c_double, C.c_double]
-            L.or_phase_hg.restype = C.c_double
-            L.or_phase_rayleigh.argtypes = [C.c_double]
-            L.or_phase_rayleigh.restype = C.c_double
-            L.or_sample_hg.argtypes = [C.c_double, C.c_double]
-            L.or_sample_hg.restype = C.c_double
-            L.or_sample_rayleigh.argtypes = [C.c_double]
-            L.or_sample_rayleigh.restype = C.c_double
-            L.or_rotate.argtypes = [_dp, C.c_double, C.c_double, _dp]
-            L.or_onb.argtypes = [_dp, _dp, _dp]
-            L.or_pixel_solid_angle.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int]
-            L.or_pixel_solid_angle.restype = C.c_double
-            L.or_transmittance.argtypes = [C.POINTER(ORScene), _fp, _dp, _dp, C.c_double]
-            L.or_transmittance.restype = C.c_double
-            L.or_intervals.argtypes = [C.POINTER(ORScene), _dp, _dp, C.c_double, _i64p, _dp, C.c_int]
-            L.or_intervals.restype = C.c_int
-            L.or_render.argtypes = [C.POINTER(ORScene), _fp, _fp, C.c_uint64, C.c_uint64, C.c_double,
-                                    _dp, _dp, _dp, _dp, _dp, _dp, _dp, _u64p, C.c_int]
-            L.or_render.restype = C.c_int
-            L.or_path.argtypes = [C.POINTER(ORScene), _fp, C.c_uint64, _dp, _dp, _i64p, _dp, C.POINTER(C.c_int)]
-            L.or_path.restype = C.c_int
-            L.or_sun_rect.argtypes = [C.POINTER(ORScene), _dp]
-            L.or_single_scatter_quad.argtypes = [C.POINTER(ORScene), _fp, C.c_int, C.c_int, _dp]
-            L.or_camera_frame.argtypes = [C.POINTER(ORScene), C.c_int, _dp]
-            L.or_surf_render.argtypes = [C.POINTER(ORSurf), C.c_double, C.c_double, C.c_uint64, C.c_uint64,
-                                         C.c_double, _dp, _dp, _dp, _dp, _dp, _u64p, _dp, _dp]
-            L.or_surf_render.restype = C.c_int
-            L.or_space_carve.argtypes = [C.POINTER(ORScene), _dp, C.c_double, C.POINTER(C.c_uint8)]
-            L.or_pixel_coords.argtypes = [C.POINTER(ORScene), C.c_int, _dp, _dp]
-            L.or_pixel_coords.restype = C.c_int
-            L.or_tally_count.restype = C.c_int
-            _lib = L
+            _lib = _load(build())
     return _lib
+
+
+@contextlib.contextmanager
+def planted(name: str):
+    """Tests only: inside the block, every call goes to a copy of the oracle
+    compiled with the planted mistake OR_PLANT_<name> (see oracle.c), so a
+    test can show that its pin rejects that mistake."""
+    global _lib
+    lib()
+    with _lock:
+        saved = _lib
+        _lib = _load(build(plant=name))
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = saved
+
+
+def _load(path):
+    L = C.CDLL(path)
+    L.or_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+    L.or_fnv1a_words.argtypes = [_u32p, C.c_int]
+    L.or_fnv1a_words.restype = C.c_uint64
+    L.or_phase_hg.argtypes = [C.c_double, C.c_double]
+    L.or_phase_hg.restype = C.c_double
+    L.or_phase_rayleigh.argtypes = [C.c_double]
+    L.or_phase_rayleigh.restype = C.c_double
+    L.or_sample_hg.argtypes = [C.c_double, C.c_double]
+    L.or_sample_hg.restype = C.c_double
+    L.or_sample_rayleigh.argtypes = [C.c_double]
+    L.or_sample_rayleigh.restype = C.c_double
+    L.or_rotate.argtypes = [_dp, C.c_double, C.c_double, _dp]
+    L.or_onb.argtypes = [_dp, _dp, _dp]
+    L.or_pixel_solid_angle.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int]
+    L.or_pixel_solid_angle.restype = C.c_double
+    L.or_transmittance.argtypes = [C.POINTER(ORScene), _fp, _dp, _dp, C.c_double]
+    L.or_transmittance.restype = C.c_double
+    L.or_intervals.argtypes = [C.POINTER(ORScene), _dp, _dp, C.c_double, _i64p, _dp, C.c_int]
+    L.or_intervals.restype = C.c_int
+    L.or_render.argtypes = [C.POINTER(ORScene), _fp, _fp, C.c_uint64, C.c_uint64, C.c_double,
+                            _dp, _dp, _dp, _dp, _dp, _dp, _dp, _u64p, C.c_int]
+    L.or_render.restype = C.c_int
+    L.or_path.argtypes = [C.POINTER(ORScene), _fp, C.c_uint64, _dp, _dp, _i64p, _dp, C.POINTER(C.c_int)]
+    L.or_path.restype = C.c_int
+    L.or_sun_rect.argtypes = [C.POINTER(ORScene), _dp]
+    L.or_single_scatter_quad.argtypes = [C.POINTER(ORScene), _fp, C.c_int, C.c_int, _dp]
+    L.or_camera_frame.argtypes = [C.POINTER(ORScene), C.c_int, _dp]
+    L.or_surf_render.argtypes = [C.POINTER(ORSurf), C.c_double, C.c_double, C.c_uint64, C.c_uint64,
+                                 C.c_double, _dp, _dp, _dp, _dp, _dp, _u64p, _dp, _dp]
+    L.or_surf_render.restype = C.c_int
+    L.or_space_carve.argtypes = [C.POINTER(ORScene), _dp, C.c_double, C.POINTER(C.c_uint8)]
+    L.or_pixel_coords.argtypes = [C.POINTER(ORScene), C.c_int, _dp, _dp]
+    L.or_pixel_coords.restype = C.c_int
+    L.or_tally_count.restype = C.c_int
+    return L
 
 
 def _ptr(a, t):
@@ -332,15 +360,25 @@ def single_scatter_quad(sc, beta, sub: int = 8, steps: int = 8):
     return img
 
 
-def adam_step(beta, m, v, grad, t, lr, b1=0.9, b2=0.999, eps=1e-8):
-    """Adam (Kingma & Ba) on beta with projection beta >= 0; fp64 numpy."""
+def adam_step(beta, m, v, grad, t, lr, b1=0.9, b2=0.999, eps=1e-8, _plant=""):
+    """Adam (Kingma & Ba, Algorithm 1) on beta with projection beta >= 0
+    (READING of the paper's "modified Adam": the projection keeps the
+    extinction physical); fp64 numpy.  Step t (1-based): moments
+    m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2, bias-corrected by
+    1 - b1^t and 1 - b2^t, step lr m_hat / (sqrt(v_hat) + eps).
+    ``_plant`` (tests only) plants a mistake: "no_bias_correction" or
+    "no_projection"."""
     beta = np.asarray(beta, dtype=np.float64)
     g = np.asarray(grad, dtype=np.float64)
     m = b1 * np.asarray(m, dtype=np.float64) + (1 - b1) * g
     v = b2 * np.asarray(v, dtype=np.float64) + (1 - b2) * g * g
     mh = m / (1 - b1 ** t)
     vh = v / (1 - b2 ** t)
-    beta = np.maximum(beta - lr * mh / (np.sqrt(vh) + eps), 0.0)
+    if _plant == "no_bias_correction":
+        mh, vh = m, v
+    beta = beta - lr * mh / (np.sqrt(vh) + eps)
+    if _plant != "no_projection":
+        beta = np.maximum(beta, 0.0)
     return beta, m, v
 
 

@@ -29,12 +29,18 @@
  *
  * Readings where the paper is silent or inconsistent are marked READING.
  * Parity status: every function here is pinned by the CPU test suite
- * (closed forms, invariants, quadrature, finite differences, brute force);
- * multiple-scattering images beyond first order have no closed form and are
- * pinned only through energy balance, unbiasedness and the FD identity.
+ * (closed forms, invariants, quadrature, finite differences, brute force).
+ * The two-type medium (cloud + air) is pinned by the first- and
+ * second-order radiance of a homogeneous slab and by the law of the first
+ * scattering angle; images beyond second order have no closed form and are
+ * pinned through energy balance, unbiasedness and the FD identity.
  *
  * Floating point: all path arithmetic is double.  Build with
  * -ffp-contract=off so results do not depend on the host's FMA contraction.
+ *
+ * Planted mistakes (OR_PLANT_* macros) exist only so that the CPU tests can
+ * show their pins reject a plausible error; oracle.build() never defines
+ * them, and the tests compile them into separate copies of this file.
  */
 #include <math.h>
 #include <stdint.h>
@@ -438,6 +444,10 @@ static int64_t project(const ocam* k, const double x[3], int* col_out, int* row_
 /* ------------------------------------------------------------------------ */
 static double fs_medium(const or_scene* s, double bc, double mu)
 {
+#ifdef OR_PLANT_AIR_BY_EXTINCTION
+    /* planted mistake (tests only): the air term weighted by its extinction */
+    return s->albedo_cloud * bc * or_phase_hg(s->hg_g, mu) + s->beta_air * or_phase_rayleigh(mu);
+#endif
     return s->albedo_cloud * bc * or_phase_hg(s->hg_g, mu) + s->albedo_air * s->beta_air * or_phase_rayleigh(mu);
 }
 static double beta_s(const or_scene* s, double bc) { return s->albedo_cloud * bc + s->albedo_air * s->beta_air; }
@@ -629,6 +639,10 @@ static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double
         /* particle type, then direction from that type's phase function */
         double bsc = s->albedo_cloud * bcv;
         int cloud = (u[1] * beta_s(s, bcv) <= bsc);
+#ifdef OR_PLANT_TYPE_BY_EXTINCTION
+        /* planted mistake (tests only): type chosen by extinction */
+        cloud = (u[1] * beta_tot(s, bc, vcol) <= bcv);
+#endif
         P->type[k] = cloud ? 0 : 1;
         double mu = cloud ? or_sample_hg(s->hg_g, u[2]) : or_sample_rayleigh(u[2]);
         or_rotate(P->om[k - 1], mu, 2.0 * OR_PI * u[3], P->om[k]);
@@ -730,6 +744,11 @@ static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
                 vert = 0.0;       /* zero weight under M_ref from here on */
             } else {
                 double fp_ref = fs_ref / beta_s(s, bref);
+#ifdef OR_PLANT_DIRECTION_PDF_BY_EXTINCTION
+                /* planted mistake (tests only): the direction pdf normalised
+                 * by the extinction, which drops the vertex's albedo */
+                fp_ref = fs_ref / beta_tot(s, br, vk);
+#endif
                 vert *= fs_medium(s, (double)bt[vk], mu) / (beta_tot(s, br, vk) * fp_ref);
             }
         }

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpathrecycle.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["pt_sample.cu", "pt_paths.cu", "pt_events.cu", "pt_batch.cu", "pt_api.cu", "pt_static.cu",
-           "pt_surf.cu"]
+           "pt_surf.cu", "pt_probes.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -30,7 +30,8 @@ def nvcc() -> str:
 
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    files.append(os.path.join(HERE, "..", "include", "pathrecycle.h"))
+    inc = os.path.join(HERE, "..", "include")
+    files.extend(os.path.join(inc, f) for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     files.append(os.path.abspath(__file__))
     return files
 

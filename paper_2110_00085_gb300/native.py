@@ -97,6 +97,7 @@ def load():
         L.batch_set_launch.argtypes = [_vp, C.c_int, C.c_int]
         L.batch_launch_limits.argtypes = [_vp, C.c_int, C.POINTER(C.c_int)]
         L.batch_free.argtypes = [_vp]
+        L.pt_probe.argtypes = [C.c_int, _vp, C.c_int64, _vp, C.c_int64, C.c_int, _vp, _vp]
         L.pt_last_error.restype = C.c_char_p
         L.pt_version.restype = C.c_char_p
         _lib = L
@@ -363,13 +364,36 @@ def render_forward_static(sc, beta: torch.Tensor, n_paths: int, seed: int, first
     n_pix = int(sum(c.width * c.height for c in sc.cameras))
     n_vox = int(sc.n[0] * sc.n[1] * sc.n[2])
     if images is None:
-        images = torch.zeros(n_pix, dtype=torch.float64, device="cuda")
+        images = torch.zeros(n_pix, dtype=torch.float64, device=beta.device)
     n_norm = float(n_paths if n_norm is None else n_norm)
     rc = load().render_forward_static(C.byref(d), _dev(beta, torch.float32, "beta", n_vox), first, n_paths, n_norm,
                                       seed, epoch, _dev(images, torch.float64, "images", n_pix),
                                       PT_ACCUMULATE if accumulate else 0, _vp(_stream(stream)))
     _check(rc, "render_forward_static")
     return images
+
+
+PROBE_GATHER_F32, PROBE_RED_F64, PROBE_RED_F64_WARP, PROBE_RED_F64_SAME, PROBE_RED_F32, PROBE_COPY = range(6)
+
+
+def probe(kind: int, buf: torch.Tensor, iters: int = 0, blocks: int = 0, src: Optional[torch.Tensor] = None,
+          sink: Optional[torch.Tensor] = None, stream=None):
+    """One memory-rate probe (include/pt_probes.h) on ``buf``: random gathers
+    or reductions (``iters`` per thread, ``blocks`` x 256 threads) or a
+    streaming copy ``src`` -> ``buf`` (16-byte elements)."""
+    if not isinstance(buf, torch.Tensor) or not buf.is_cuda or not buf.is_contiguous():
+        raise TypeError("probe: buf must be a contiguous CUDA tensor")
+    esz = 16 if kind == PROBE_COPY else (8 if kind in (PROBE_RED_F64, PROBE_RED_F64_WARP, PROBE_RED_F64_SAME)
+                                          else 4)
+    n = buf.numel() * buf.element_size() // esz
+    sp = None
+    if src is not None:
+        if not src.is_cuda or src.numel() * src.element_size() < n * esz:
+            raise ValueError("probe: src must be a CUDA tensor at least as large as buf")
+        sp = src.data_ptr()
+    rc = load().pt_probe(int(kind), buf.data_ptr(), n, sp, int(iters), int(blocks),
+                         None if sink is None else _dev(sink, torch.float32, "sink"), _vp(_stream(stream)))
+    _check(rc, "pt_probe")
 
 
 class Batch:

@@ -9,10 +9,12 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "pathrecycle.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
-def _declared():
-    src = open(HEADER).read()
+def _declared(headers=None):
+    src = "\n".join(open(h).read() for h in (headers or HEADERS))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
     return sorted(set(n for n in names if n not in ("if", "sizeof")))
@@ -81,6 +83,20 @@ def test_oracle_is_not_imported_by_the_package():
                 assert "oracle.c" not in txt, f
 
 
+def test_probe_arguments_are_checked_without_a_gpu():
+    """pt_probe refuses unknown kinds, null buffers and sizes that are not a
+    power of two before it launches anything."""
+    from paper_2110_00085_gb300 import native as N
+    L = N.load()
+    assert L.pt_probe(99, None, 0, None, 1, 1, None, None) == 1
+    assert L.pt_probe(0, None, 1024, None, 1, 1, None, None) == 1
+    assert b"null" in L.pt_last_error()
+    assert L.pt_probe(1, C.c_void_p(16), 1000, None, 1, 1, None, None) == 1
+    assert b"power of two" in L.pt_last_error()
+    assert L.pt_probe(0, C.c_void_p(16), 1024, None, 8, 1, None, None) == 1
+    assert b"sink" in L.pt_last_error()
+
+
 def test_surface_entry_points_reject_null_arguments_without_a_gpu():
     from paper_2110_00085_gb300 import native as N
     L = N._surf_lib()
@@ -94,15 +110,17 @@ def test_surface_entry_points_reject_null_arguments_without_a_gpu():
 
 
 def test_header_is_plain_c(tmp_path):
-    """include/pathrecycle.h is a C header: it compiles as C11 with warnings as
-    errors (no C++ or CUDA types in the boundary)."""
+    """include/pathrecycle.h and include/pt_probes.h are C headers: they
+    compile as C11 with warnings as errors (no C++ or CUDA types in the
+    boundary)."""
     import shutil
     import subprocess
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
     src = tmp_path / "t.c"
-    src.write_text('#include "pathrecycle.h"\nint main(void) { pt_scene* s = 0; (void)s; return PT_OK; }\n')
+    src.write_text('#include "pathrecycle.h"\n#include "pt_probes.h"\n'
+                   'int main(void) { pt_scene* s = 0; (void)s; return PT_OK + PT_PROBE_GATHER_F32; }\n')
     r = subprocess.run([cc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), "-c",
                         str(src), "-o", str(tmp_path / "t.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
