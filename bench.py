@@ -325,6 +325,13 @@ def measure_peaks(dev, reps: int = 10, warmup: int = 3):
                      "gbs": ops * esz / (ms * 1e-3) / 1e9, "ms_best": ms, "ms_median": med,
                      "buffer_mb": n * esz / 2 ** 20}
         del buf, sink
+    for name, kind, iters in (("shared_f32_atomic", 6, 1 << 12), ("shared_f32_atomic_run4", 7, 1 << 12),
+                              ("shared_u32_atomic", 8, 1 << 12), ("shared_f64_atomic", 9, 1 << 12)):
+        buf = torch.zeros(blocks * 256, dtype=torch.float32, device=dev)
+        ms, med = best_ms(lambda: N.probe(kind, buf, iters, blocks))
+        ops = blocks * 256 * iters
+        out[name] = {"rate": ops / (ms * 1e-3), "unit": "atomics/s", "ms_best": ms, "ms_median": med,
+                     "table_kb": 16}
     n16 = 1 << 28   # 4 GiB each way
     src = torch.empty(n16 * 4, dtype=torch.float32, device=dev).fill_(1.0)
     dst = torch.empty_like(src)
@@ -389,56 +396,114 @@ def profiled_traffic(call, n):
     return float(rec["bytes_per_call"]) * n / float(rec["paths"])
 
 
-def calibrate_matched(args, ws, scene, gt_img, beta0, n, lr, seed, reuse_ms):
-    """Resample budget of equal gradient error and its step time.
-
-    One recycling window is run after a first window (as in the timed
-    region), with an independent second path set giving the reuse error per
-    step; fresh-path errors are swept over budgets n/8 .. n at every
-    extinction of that window; n* solves e_resample(n*) = e_reuse (both RMS
-    over the window) on the fitted log-log line, and the Alg. 1 step is
-    timed at n* (capped at 2n)."""
+def _time_steps(ws, rec, steps, warmup):
+    """CUDA-event time per Adam step of a Reconstruction (after warm-up)."""
     import torch
+    for _ in range(max(1, warmup)):
+        rec.step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        rec.step()
+    b.record()
+    torch.cuda.synchronize()
+    return max_over_ranks(ws, a.elapsed_time(b) / steps)
+
+
+MATCH_AGES = (1, 5, 9)
+
+
+def calibrate_matched(args, ws, scene, gt_img, beta0, n, lr, seed, reuse_ms):
+    """Resample budgets of equal gradient error.
+
+    After a first recycling window, a second one is run with the cached
+    gradient; at ages 1, 5 and 9 of it the reuse gradient at beta_t is
+    compared with g_ref(beta_t), the mean of 16 fresh gradients of 4N paths
+    each: e = ||g - g_ref|| / ||g_ref||, in L2 and in L1.  Fresh-path
+    gradients at N/8 .. N (two draws each) at the same extinctions give
+    e_resample(n'); n* solves e_resample(n*) = e_reuse on the fitted log-log
+    line, per norm, and the Alg. 1 step is timed at each n* (capped at 2N).
+    Neither norm is the headline: both are reported side by side."""
     from paper_2110_00085_gb300 import calibrate as CAL
     from paper_2110_00085_gb300.driver import Reconstruction
 
     rc = Reconstruction(scene, gt_img, beta0, n, n_r=N_R, lr=lr, seed=seed, cache=True)
     for _ in range(N_R):
         rc.step()
-    er = CAL.reuse_errors(rc, seed_b=seed + 7777)
-    rc.paths.close()
-    budgets = [n // 8, n // 4, n // 2, n]
-    # the same extinctions as the reuse errors: every step of the window
-    es, es2 = CAL.resample_errors_both(scene, gt_img, er["betas"], budgets)
-    fit = CAL.n_star(er["rms"], es)
-    fit2 = CAL.n_star(er["rms_l2"], es2)
-    n_star = int(min(max(round(fit["n_star"]), 1024), 2 * n))
-    res = Reconstruction(scene, gt_img, beta0, n_star, n_r=1, lr=lr, seed=seed, cache=True)
-    for _ in range(max(1, args.warmup)):
-        res.step()
-    torch.cuda.synchronize()
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(args.steps):
-        res.step()
-    b.record()
-    torch.cuda.synchronize()
-    ms_star = max_over_ranks(ws, a.elapsed_time(b) / args.steps)
-    res.paths.close()
-    return {"window": f"Adam steps {N_R}-{2 * N_R - 1} (paths stored at step {N_R})",
-            "error": "L1 spread of two independent gradient estimates (mean over voxels of |g_a - g_b|), "
-                     "RMS over the window",
-            "e_reuse": er["rms"], "e_reuse_per_step": [float(f"{e:.5g}") for e in er["per_step"]],
-            "l2": {"e_reuse": er["rms_l2"], "e_resample": {str(k): v for k, v in es2.items()},
-                   "loglog_slope": fit2["slope"], "n_star_fit": fit2["n_star"],
-                   "signal_norm_mean": sum(er["signal"]) / len(er["signal"])},
-            "e_resample": {str(k): v for k, v in es.items()}, "loglog_slope": fit["slope"],
-            "n_star": n_star, "n_star_fit": fit["n_star"], "capped": fit["n_star"] > 2 * n,
-            "reuse_ms_per_step": reuse_ms, "resample_ms_per_step_at_n_star": ms_star,
-            "reuse_speedup": ms_star / reuse_ms,
-            "fresh_equivalent_paths_per_s": {"reuse": ws * n_star / (reuse_ms * 1e-3),
-                                             "resample": ws * n_star / (ms_star * 1e-3)}}
+    m = CAL.matched_errors(rc, [n // 8, n // 4, n // 2, n], MATCH_AGES)
+    rc.close()
+    out = {"window": f"Adam steps {N_R}-{2 * N_R - 1} (paths stored at step {N_R}), ages {list(MATCH_AGES)}",
+           "error": "||g - g_ref|| / ||g_ref||, g_ref = mean of 16 fresh gradients of 4N paths at the same "
+                    "extinction; RMS over the ages (and 2 fresh draws per budget)",
+           "errors": m, "reuse_ms_per_step": reuse_ms, "norms": {}}
+    for norm in ("l2", "l1"):
+        fit = m[f"n_star_{norm}"]
+        ns = int(min(max(round(fit), 1024), 2 * n))
+        res = Reconstruction(scene, gt_img, beta0, ns, n_r=1, lr=lr, seed=seed, cache=True)
+        ms_star = _time_steps(ws, res, args.steps, args.warmup)
+        res.close()
+        out["norms"][norm] = {"e_reuse": m["reuse"][norm],
+                              "e_resample": {k: v[norm] for k, v in m["resample"].items()},
+                              "loglog_slope": m[f"slope_{norm}"], "n_star_fit": fit, "n_star": ns,
+                              "capped": fit > 2 * n, "resample_ms_per_step_at_n_star": ms_star,
+                              "reuse_speedup": ms_star / reuse_ms,
+                              "fresh_equivalent_paths_per_s": {"reuse": ws * ns / (reuse_ms * 1e-3),
+                                                               "resample": ws * ns / (ms_star * 1e-3)}}
+    return out
+
+
+def ablation(args, ws, scene, gt_img, beta_gt, beta0, n, lr, seed, steps=50):
+    """Norm-free comparison of Alg. 2 (N_r = 10) and Alg. 1 (N_r = 1), the
+    volume analogue of the paper's recycling ablation (Sec. 6): the same
+    start, path budget and step size, ``steps`` Adam steps each; per step
+    the loss of the step's own images and eps = sum|beta - beta_gt| /
+    sum beta_gt against the cumulative CUDA-event time of the steps."""
+    import torch
+    from paper_2110_00085_gb300.driver import Reconstruction
+
+    gsum = float(beta_gt.double().sum())
+    arms = {}
+    for n_r in (N_R, 1):
+        rec = Reconstruction(scene, gt_img, beta0, n, n_r=n_r, lr=lr, seed=seed, cache=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
+        loss = torch.zeros(steps, dtype=torch.float64, device=beta0.device)
+        eps = torch.zeros(steps, dtype=torch.float64, device=beta0.device)
+        torch.cuda.synchronize()
+        for k in range(steps):
+            ev[2 * k].record()
+            rec.step()
+            ev[2 * k + 1].record()
+            loss[k] = rec.loss[0]
+            eps[k] = (rec.beta.double() - beta_gt.double()).abs().sum() / gsum
+        torch.cuda.synchronize()
+        t = 0.0
+        ts = []
+        for k in range(steps):
+            t += ev[2 * k].elapsed_time(ev[2 * k + 1]) * 1e-3
+            ts.append(t)
+        rec.close()
+        arms[f"n_r={n_r}"] = {"t_s": [float(f"{x:.4g}") for x in ts],
+                              "loss": [float(f"{x:.4g}") for x in loss.cpu().tolist()],
+                              "eps": [float(f"{x:.4g}") for x in eps.cpu().tolist()]}
+    a, b = arms[f"n_r={N_R}"], arms["n_r=1"]
+
+    def first_time(arm, key, level):
+        for t, v in zip(arm["t_s"], arm[key]):
+            if v <= level:
+                return t
+        return None
+
+    summary = {}
+    for key in ("eps", "loss"):
+        level = max(min(a[key]), min(b[key]))   # a level both arms reach
+        ta, tb = first_time(a, key, level), first_time(b, key, level)
+        summary[key] = {"level_both_reach": level, f"t_s_n_r={N_R}": ta, "t_s_n_r=1": tb,
+                        "speedup_reuse": (tb / ta) if ta and tb else None,
+                        f"final_n_r={N_R}": a[key][-1], "final_n_r=1": b[key][-1]}
+    return {"steps": steps, "lr": lr, "n_paths": n, "start": "uniform mean of the true field (reading R11)",
+            "arms": arms, "summary": summary}
 
 
 def run_recon(args, ws, rank, local):
@@ -623,6 +688,89 @@ def run_surfaces(args, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def rooflines(avg, dom, T, info, n, n_cams, probes, dev):
+    """Achieved rates of the passes against the measured peaks.
+
+    Algorithmic work per call, from the tallies of the stored path set:
+    every voxel crossing (of a stored flight or a shadow ray) is one 4-byte
+    extinction gather in the recycled forward pass and one 8-byte FP64
+    addition into the gradient in render_grad; HBM bytes are the stored
+    records (32 B + 4 B record-to-event map per record), events (32 B, plus
+    4 B per-event scalar) and the contribution cache (4 B per event and
+    camera) each pass streams.  The main roofline is the dominant call's L2
+    view: for render_grad the FP64 additions against the L2 reduction rate
+    of 32 lanes on 32 consecutive doubles (each lane its own address, the
+    best case of distinct-address reductions); the kernel merges same-voxel
+    terms of adjacent lanes before its reductions, so against the
+    random-address rate its fraction exceeds 1."""
+    import torch
+    pk, pk_src = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    cross = {"paths_reweight": T["shadow_cross"] + T["seg_cross"], "render_grad": T["shadow_cross"] + T["seg_cross"],
+             "paths_store": T["seg_cross"]}
+    n_rec = float(info["n_records"])
+    n_ev = float(info["n_records"] - info["n_stored"])
+    hbm_bytes = {"paths_reweight": 36 * n_rec + 4 * n_ev + 32 * n_ev + 4 * n_cams * n_ev,
+                 "render_grad": 36 * n_rec + (40 + 4 * n_cams) * n_ev,
+                 "paths_store": 64 * n_rec + 36 * n_ev}
+    # the voxel traversal's ALU-pipe lane operations per crossing, counted
+    # step by step: next face = min of three (2), clipped segment length (2),
+    # end test (1), axis choice (3), per-axis counter selects (3), index step
+    # select and add (3), running t (1), bounds test (1)
+    alu_per_cross = 16.0
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    alu_peak = sms * 64 * sm_mhz * 1e6 / 1e12     # SMs x 4 partitions x 16 ALU lanes per clock
+    hbm_peak = pk.get("hbm_gbs", 6800.0)
+    views = {}
+    for call, ms in avg.items():
+        t = ms * 1e-3
+        v = {"ms": round(ms, 3), "crossings": cross.get(call)}
+        if call == "render_grad":
+            a = 8 * cross[call] / t / 1e9
+            v["l2_fp64_add"] = {"achieved": a, "unit": "GB/s",
+                                "peak_warp_coalesced": probes["red_f64_warp_l2"]["gbs"],
+                                "frac_warp_coalesced": a / probes["red_f64_warp_l2"]["gbs"],
+                                "peak_random": probes["red_f64_random_l2"]["gbs"],
+                                "frac_random": a / probes["red_f64_random_l2"]["gbs"]}
+        if call == "paths_reweight":
+            a = 4 * cross[call] / t / 1e9
+            v["l2_gather"] = {"achieved": a, "unit": "GB/s", "peak_random": probes["gather_f32_l2"]["gbs"],
+                              "frac_random": a / probes["gather_f32_l2"]["gbs"],
+                              "note": "most gathers hit L1 (neighbouring shadow rays share cache lines), so the "
+                                      "random-gather L2 rate is exceeded"}
+        if call in hbm_bytes:
+            a = hbm_bytes[call] / t / 1e9
+            v["hbm"] = {"achieved": a, "unit": "GB/s", "peak": hbm_peak, "frac": a / hbm_peak,
+                        "bytes": hbm_bytes[call]}
+        if call in cross:
+            a = alu_per_cross * cross[call] / t / 1e12
+            v["alu"] = {"achieved": a, "unit": "Tops/s", "peak": alu_peak, "frac": a / alu_peak}
+        views[call] = v
+    traffic = profiled_traffic(dom, n)
+    if dom == "render_grad":
+        g = views[dom]["l2_fp64_add"]
+        main = {"bound": "l2", "kernel": "render_grad (k_event_grad + k_path_grad)", "achieved": g["achieved"],
+                "peak": g["peak_warp_coalesced"], "unit": "GB/s", "frac": g["frac_warp_coalesced"],
+                "traffic": traffic,
+                "work": f"8 B FP64 addition per voxel crossing x {cross[dom]:.3e} crossings per call",
+                "peak_source": "measured in this run: pt_probe FP64 reductions, 32 lanes on 32 consecutive doubles "
+                               f"of a 16 MB grid, {sms} SMs x 8 blocks of 256 threads, best of 10",
+                "frac_random_address_peak": g["frac_random"]}
+    else:
+        vv = views[dom]
+        key = "l2_gather" if "l2_gather" in vv else "hbm"
+        g = vv[key]
+        pkv = g.get("peak_random", g.get("peak"))
+        main = {"bound": "l2" if key == "l2_gather" else "hbm", "kernel": dom, "achieved": g["achieved"],
+                "peak": pkv, "unit": "GB/s", "frac": g["achieved"] / pkv, "traffic": traffic}
+    if traffic is not None:
+        main["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernels at 2^20 "
+                                  "paths (profiles/traffic_render_grad_noise128.txt), scaled by paths")
+    main["hbm_peak_source"] = f"{pk_src} ({'MEASURED_PEAKS.json' if pk_src == 'measured' else 'fallback'})"
+    return {"main": main, "views": views}
+
+
 def run_native(args, ws, rank, local):
     import numpy as np
     import torch
@@ -633,6 +781,8 @@ def run_native(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    # the memory rates the passes are bounded by, measured on this device
+    probes = measure_peaks(dev)
     sc, gt_np, beta0_np = workload(args.paths)
     n = sc.n_paths
     scene = N.Scene(sc, scene_id=rank)
@@ -730,36 +880,16 @@ def run_native(args, ws, rank, local):
         torch.cuda.synchronize()
     e2e_s = max_over_ranks(ws, (time.perf_counter() - w0) / args.steps)
 
-    # ---- roofline of the dominant kernel ----
+    # ---- rooflines: L2 (the dominant bound), HBM and ALU views per call ----
     avg = {k: sum(v) / len(v) for k, v in kern.items() if v}
     tot = {k: sum(v) for k, v in kern.items()}
     dom = max(tot, key=tot.get)
-    pk, pk_src = peaks()
-    seg_x = T["seg_cross"]
-    shd_x = T["shadow_cross"]
-    # The voxel traversal is bound by the ALU pipe (compares, selects,
-    # min/max, integer index updates; the FMA pipe carries the rest).  Its
-    # algorithmic ALU work per voxel crossing, counted step by step:
-    # next face = min of three (2), clipped segment length (2), end test (1),
-    # axis choice (3), per-axis counter selects (3), index step select and
-    # add (3), running t (1), bounds test (1) = 16 lane operations.
-    alu_per_cross = 16.0
-    crosses = {"paths_reweight": shd_x + seg_x, "render_grad": shd_x + seg_x,
-               "paths_store": seg_x}[dom]
-    achieved = alu_per_cross * crosses / (avg[dom] * 1e-3) / 1e12      # T ALU lane-ops/s
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    peak = 152 * 64 * sm_mhz * 1e6 / 1e12   # 152 SMs x 4 partitions x 16 ALU lanes per clock
-    traffic = profiled_traffic(dom, n)
-    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": traffic,
-            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernels at 2^20 "
-                               "paths (profiles/traffic_render_grad_noise128.txt), scaled by paths")
-                              if traffic is not None else None,
-            "peak_source": f"derived: 152 SMs x 64 ALU-pipe lanes/clock x {sm_mhz:.0f} MHz ({pk_src} max SM clock)",
-            "work": f"{alu_per_cross:.0f} ALU ops per voxel crossing x {crosses:.3e} crossings per call",
-            "per_call_ms": {k: round(v, 3) for k, v in avg.items()},
-            "alu_frac_by_call": {k: round(alu_per_cross * (shd_x + seg_x if k != "paths_store" else seg_x)
-                                          / (v * 1e-3) / 1e12 / peak, 4) for k, v in avg.items()}}
+    roof = rooflines(avg, dom, T, info, n, len(sc.cameras), probes, dev)
+
+    # ---- the recycling ablation (norm-free): Alg. 2 vs Alg. 1 in time ----
+    abl = None
+    if not args.no_calibration:
+        abl = ablation(args, ws, scene, gt_img, beta_gt, beta0, n, lr, sc.seed + rank, steps=args.ablation_steps)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -782,8 +912,11 @@ def run_native(args, ws, rank, local):
         "resample": {"ms_per_step": ms_res, "value": ws * n / (ms_res * 1e-3), "unit": UNIT,
                      "note": "Alg. 1 at the same path budget"},
         "matched_error": matched,
+        "ablation": abl,
         "kernels_ms": {k: round(v, 3) for k, v in avg.items()},
-        "roofline": roof,
+        "roofline": roof["main"],
+        "roofline_views": roof["views"],
+        "peaks": probes,
         "cpu_baseline": cpu,
         "e2e": {"value": ws * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": gt_img.numel() * 8,
                 "d2h_bytes_per_step": 8},
@@ -803,7 +936,9 @@ def main():
     ap.add_argument("--paths", type=int, default=None, help="override the path budget (tests only)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--no-calibration", action="store_true", help="skip the matched-gradient-error arm")
+    ap.add_argument("--no-calibration", action="store_true",
+                    help="skip the matched-gradient-error arm and the recycling ablation")
+    ap.add_argument("--ablation-steps", type=int, default=50, help="Adam steps per arm of the recycling ablation")
     ap.add_argument("--workload", default="noise128", choices=["noise128", "batch", "recon", "surfaces", "peaks"])
     ap.add_argument("--surf-steps", type=int, default=800, help="surfaces workload: Adam steps per arm")
     ap.add_argument("--path-scale", type=int, default=0, help="batch workload: lower every 2^k path budget by k")

@@ -188,10 +188,26 @@ int paths_reweight(pt_paths* paths, const float* beta_t, double* images,
  * score_v.  dL_dI: device, images layout (e.g. F - I_gt); grad: device,
  * nx*ny*nz doubles, zeroed first unless PT_ACCUMULATE.  With PT_CACHE the
  * contributions come from the latest paths_reweight (which must have been
- * called with PT_CACHE and the same beta_t).
+ * called with PT_CACHE and the same beta_t, unchanged since): a call whose
+ * beta_t is another buffer than that reweight's, or that no
+ * paths_reweight(PT_CACHE) preceded since the latest store, is refused
+ * with PT_E_INVALID before anything is launched.  (The library cannot see
+ * a grid changed in place; paths_cache_token tells callers which reweight
+ * the cache holds.)
  */
 int render_grad(pt_paths* paths, const float* beta_t, const double* dL_dI,
                 double* grad, uint32_t flags, void* stream);
+
+/*
+ * paths_cache_token -- which paths_reweight(PT_CACHE) the handle's
+ * contribution cache holds: a number that changes with every such call on
+ * any handle, or 0 when the cache is invalid (no such call since the latest
+ * store).  A caller that keeps the token of its reweight can tell whether a
+ * later render_grad(PT_CACHE) would read that reweight's contributions
+ * (differentiation through several forward passes before one backward).
+ * Host only; never fails (0 for a null handle).
+ */
+uint64_t paths_cache_token(const pt_paths* paths);
 
 int paths_free(pt_paths* paths);
 /* Synchronises the stream; fills counts of the latest store. */

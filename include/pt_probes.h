@@ -30,7 +30,11 @@ enum {
     PT_PROBE_RED_F64_SAME = 3, /* FP64 reductions, the 32 lanes of a warp on one random address     */
     PT_PROBE_RED_F32 = 4,      /* FP32 reductions at random indices (float32[n])                     */
     PT_PROBE_COPY = 5,         /* streaming copy src -> buf of n 16-byte elements (HBM when large)   */
-    PT_PROBE_KINDS = 6
+    PT_PROBE_SHARED_F32 = 6,   /* FP32 atomic adds into a 4096-entry shared-memory table, random slots */
+    PT_PROBE_SHARED_F32_RUN4 = 7, /* the same, lanes in groups of 4 on one slot                       */
+    PT_PROBE_SHARED_U32 = 8,   /* 32-bit integer atomic adds, random slots                          */
+    PT_PROBE_SHARED_F64 = 9,   /* FP64 atomic adds into a 2048-entry shared table, random slots      */
+    PT_PROBE_KINDS = 10
 };
 
 /*
@@ -39,9 +43,13 @@ enum {
  * congruential sequence, so accesses are independent of loaded values);
  * PT_PROBE_COPY copies all n elements once (grid-stride; `iters` unused).
  *   buf   device buffer: float32[n] (GATHER, RED_F32), double[n] (RED_F64*),
- *         16-byte elements[n] (COPY destination).  The reduction probes add
- *         into it (its values change); the gather probe only reads it.
- *   n     elements of buf; a power of two >= 32 for the random kinds.
+ *         16-byte elements[n] (COPY destination), float32[blocks * 256]
+ *         (SHARED_*: each thread writes one value read back from its
+ *         block's table, so the adds are not optimised away).  The
+ *         reduction probes add into it (its values change); the gather
+ *         probe only reads it.
+ *   n     elements of buf; a power of two >= 32 for the random kinds
+ *         (SHARED_*: at least blocks * 256).
  *   src   COPY only: the source, 16-byte elements[n]; NULL otherwise.
  *   sink  GATHER only: float32[blocks * 256], one sum per thread (keeps the
  *         loads from being optimised away); NULL otherwise.

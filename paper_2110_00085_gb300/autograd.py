@@ -27,6 +27,7 @@ class RenderFn(torch.autograd.Function):
         images = paths.reweight(b.reshape(-1), cache=cache)
         ctx.paths = paths
         ctx.cache = cache
+        ctx.token = paths.cache_token() if cache else 0
         ctx.shape = beta.shape
         ctx.save_for_backward(b)
         return images
@@ -35,7 +36,10 @@ class RenderFn(torch.autograd.Function):
     def backward(ctx, grad_images: torch.Tensor):
         (b,) = ctx.saved_tensors
         gi = grad_images.detach().to(torch.float64).contiguous()
-        g = ctx.paths.grad(b.reshape(-1), gi, cache=ctx.cache)
+        # the cache serves only if it still holds this forward's contributions
+        # (another forward on the same paths replaces it): else re-trace
+        use_cache = ctx.cache and ctx.paths.cache_token() == ctx.token
+        g = ctx.paths.grad(b.reshape(-1), gi, cache=use_cache)
         return g.to(torch.float32).reshape(ctx.shape), None, None
 
 

@@ -1,6 +1,12 @@
 """Gradient error of path reuse vs resampling, and the resample path budget
 of equal error (Sec. 5: recycled paths trade variance for speed).
 
+matched_errors measures both estimators against a reference gradient
+g_ref (the mean of 16 fresh gradients of 4N paths each) as
+||g - g_ref|| / ||g_ref||, in L2 and in L1, at extinctions of one recycling
+window; the functions below it measure the spread of two independent
+estimates instead (no reference needed):
+
 Both estimators are unbiased up to the correlation of a gradient with the
 images of the same paths, so their error is measured as their spread: the
 difference of two estimates from independent path sets at the same
@@ -127,6 +133,102 @@ def resample_errors_both(scene: N.Scene, gt: torch.Tensor, betas: Sequence[torch
         out2[int(n)] = math.sqrt(a2 / len(betas))
     p.close()
     return out1, out2
+
+
+def rel_errors(g: torch.Tensor, g_ref: torch.Tensor) -> Dict[str, float]:
+    """||g - g_ref|| / ||g_ref|| in L2 and in L1."""
+    d = (g - g_ref).double()
+    r = g_ref.double()
+    return {"l2": math.sqrt(float(torch.dot(d, d)) / max(float(torch.dot(r, r)), 1e-300)),
+            "l1": float(d.abs().sum()) / max(float(r.abs().sum()), 1e-300)}
+
+
+def tail_share(g: torch.Tensor, g_ref: torch.Tensor, frac: float = 1e-3) -> float:
+    """Share of ||g - g_ref||^2 carried by the largest ``frac`` of the voxels'
+    squared errors (near frac for a light-tailed error, near 1 when a few
+    voxels carry it)."""
+    d2 = ((g - g_ref).double()) ** 2
+    k = max(1, int(frac * d2.numel()))
+    tot = float(d2.sum())
+    return float(torch.topk(d2, k).values.sum()) / tot if tot > 0 else 0.0
+
+
+def reference_gradient(scene: N.Scene, gt: torch.Tensor, beta: torch.Tensor, n: int, copies: int = 16,
+                       factor: int = 4, seed: int = 70001, epoch: int = 0, chunk: int = 0) -> torch.Tensor:
+    """g_ref(beta): the mean of ``copies`` independent resampled gradients,
+    each of ``factor`` x n fresh paths (residual and derivative from the
+    same paths, as in the timed step), stored in chunks of ``chunk`` paths
+    (default n) normalised by the total."""
+    from .driver import ChunkedPaths
+    cp = ChunkedPaths(scene, chunk=chunk or n)
+    img = scene.new_images()
+    dldi = torch.zeros_like(img)
+    g = torch.zeros(scene.n_voxels, dtype=torch.float64, device=img.device)
+    acc = torch.zeros_like(g)
+    for k in range(copies):
+        cp.store(beta, factor * n, seed + k, epoch=epoch)
+        cp.reweight(beta, img, cache=True)
+        N.loss_residual(img, gt, dldi)
+        cp.grad(beta, dldi, g, cache=True)
+        acc += g
+    cp.close()
+    return acc / copies
+
+
+def matched_errors(rec, n_fresh: Sequence[int], ages: Sequence[int], copies: int = 16, factor: int = 4,
+                   fresh_draws: int = 2, seed: int = 70001) -> Dict:
+    """The reuse and resample gradient errors against a reference gradient.
+
+    ``rec`` (a driver.Reconstruction at a resample boundary, cached
+    gradient) runs one recycling window; at each age k in ``ages`` its own
+    gradient at beta_t (paths stored k steps earlier) is kept.  Then, per
+    kept extinction, g_ref = the mean of ``copies`` fresh gradients of
+    ``factor`` x N paths, the reuse error e = ||g - g_ref|| / ||g_ref||, and
+    the same error of ``fresh_draws`` fresh-path gradients at each budget of
+    ``n_fresh``.  Errors are RMS over the kept ages (and draws), in L2 and in
+    L1; with the share of the squared error carried by the largest 0.1% of
+    voxels (how heavy the error's tail is)."""
+    if rec.t % rec.n_r != 0:
+        raise ValueError("matched_errors starts at a resample boundary")
+    scene = rec.scene
+    kept = []
+    for k in range(rec.n_r):
+        beta_t = rec.beta.clone()
+        rec.step()
+        if k in ages:
+            kept.append((k, beta_t, rec.grad.clone()))
+    p = N.Paths(scene)
+    img = scene.new_images()
+    dldi = torch.zeros_like(img)
+    gf = torch.zeros(scene.n_voxels, dtype=torch.float64, device=img.device)
+    reuse = {"l2": [], "l1": [], "tail": []}
+    fresh = {int(m): {"l2": [], "l1": [], "tail": []} for m in n_fresh}
+    refnorm = []
+    for j, (k, b, g) in enumerate(kept):
+        g_ref = reference_gradient(scene, rec.gt, b, rec.n_paths, copies, factor, seed + 1000 * j, epoch=j)
+        refnorm.append(float(g_ref.double().norm()))
+        e = rel_errors(g, g_ref)
+        reuse["l2"].append(e["l2"]); reuse["l1"].append(e["l1"]); reuse["tail"].append(tail_share(g, g_ref))
+        for m in n_fresh:
+            for r in range(fresh_draws):
+                _fresh_grad(p, b, rec.gt, int(m), seed + 500 + 17 * r, 100 + j, img, dldi, gf)
+                e = rel_errors(gf, g_ref)
+                f = fresh[int(m)]
+                f["l2"].append(e["l2"]); f["l1"].append(e["l1"]); f["tail"].append(tail_share(gf, g_ref))
+    p.close()
+    rms = lambda v: math.sqrt(sum(x * x for x in v) / len(v))
+    mean = lambda v: sum(v) / len(v)
+    out = {"ages": [k for k, _, _ in kept], "copies": copies, "factor": factor, "fresh_draws": fresh_draws,
+           "ref_norm_l2": refnorm,
+           "reuse": {"l2": rms(reuse["l2"]), "l1": rms(reuse["l1"]), "tail_share_top0.1pct": mean(reuse["tail"]),
+                     "l2_per_age": reuse["l2"], "l1_per_age": reuse["l1"]},
+           "resample": {str(m): {"l2": rms(f["l2"]), "l1": rms(f["l1"]), "tail_share_top0.1pct": mean(f["tail"])}
+                        for m, f in fresh.items()}}
+    for norm in ("l2", "l1"):
+        fit = n_star(out["reuse"][norm], {m: out["resample"][str(m)][norm] for m in fresh})
+        out[f"n_star_{norm}"] = fit["n_star"]
+        out[f"slope_{norm}"] = fit["slope"]
+    return out
 
 
 def n_star(e_target: float, errors: Dict[int, float]) -> Dict:

@@ -4,6 +4,7 @@
 // Adam).  Every call launches on the caller's stream; errors are returned,
 // never raised, and described by pt_last_error().
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -148,8 +149,9 @@ __global__ void k_adam_dev(float* __restrict__ beta, float* __restrict__ m, floa
     }
 }
 
-unsigned grid_for(int64_t n, int bs, int cap = 152 * 32) {
+unsigned grid_for(int64_t n, int bs, int per_sm = 32) {
     int64_t g = (n + bs - 1) / bs;
+    const int64_t cap = (int64_t)device_sms() * per_sm;
     if (g > cap) g = cap;
     return (unsigned)(g < 1 ? 1 : g);
 }
@@ -177,6 +179,22 @@ struct pt_scene {
     int64_t n_pixels = 0;
 };
 
+int pt::device_sms() {
+    static std::atomic<int> sms[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    int v = sms[dev].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+            cudaGetLastError();
+            v = 1;
+        }
+        sms[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
 const DevCam* pt::scene_cams(const pt_scene* sc) { return sc->d_cams; }
 const float* pt::scene_omega(const pt_scene* sc) { return sc->d_omega; }
 
@@ -198,9 +216,23 @@ struct pt_paths {
     uint64_t cache_cap = 0;    // floats
     uint64_t bytes = 0;
     bool cache_valid = false;
+    uint64_t cache_token = 0;          // token of the reweight the cache holds (0: none)
+    const float* cache_beta = nullptr; // that reweight's extinction grid
 };
 
 namespace {
+// tokens of cache-writing reweights, unique over all handles of the process
+uint64_t next_cache_token() {
+    static std::atomic<uint64_t> counter{0};
+    return ++counter;
+}
+
+void set_cache(pt_paths* p, bool valid, const float* beta_t) {
+    p->cache_valid = valid;
+    p->cache_token = valid ? next_cache_token() : 0;
+    p->cache_beta = valid ? beta_t : nullptr;
+}
+
 // Stream-ordered pool of this library for the transient buffers of
 // paths_store (one per device, created on first use).  It keeps the memory
 // it has mapped (release threshold: unlimited), so repeated stores reuse it
@@ -497,7 +529,7 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
     }
     p->n = n;
     p->inv_norm = (float)(1.0 / n_norm);
-    p->cache_valid = false;
+    set_cache(p, false, nullptr);
     *pp = p;
 
     // no path kernel runs on an extinction grid with NaN, infinite or negative
@@ -619,7 +651,7 @@ int paths_reweight(pt_paths* p, const float* beta_t, double* images, uint32_t fl
     if (!(flags & PT_ACCUMULATE)) PT_CUDA(cudaMemsetAsync(images, 0, sizeof(double) * sc->n_pixels, st));
     launch_delta(beta_t, p->beta_ref, p->dbeta, p->V, st);
     launch_reweight(sc->ds, sorted_view(p), p->ev, beta_t, p->beta_ref, p->dbeta, images, cache, st);
-    p->cache_valid = (flags & PT_CACHE) != 0;
+    set_cache(p, (flags & PT_CACHE) != 0, beta_t);
     return launch_status("paths_reweight");
 }
 
@@ -629,6 +661,8 @@ int render_grad(pt_paths* p, const float* beta_t, const double* dldi, double* gr
     if (p->n == 0) return fail(PT_E_INVALID, "render_grad: handle holds no paths");
     if ((flags & PT_CACHE) && !p->cache_valid)
         return fail(PT_E_INVALID, "render_grad: PT_CACHE without a preceding paths_reweight(PT_CACHE)");
+    if ((flags & PT_CACHE) && p->cache_beta != beta_t)
+        return fail(PT_E_INVALID, "render_grad: PT_CACHE with another extinction grid than the cached reweight's");
     cudaStream_t st = S_(stream);
     const pt_scene* sc = p->scene;
     if (!(flags & PT_ACCUMULATE)) PT_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * p->V, st));
@@ -637,6 +671,8 @@ int render_grad(pt_paths* p, const float* beta_t, const double* dldi, double* gr
                 (flags & PT_CACHE) ? p->cache : nullptr, st);
     return launch_status("render_grad");
 }
+
+uint64_t paths_cache_token(const pt_paths* p) { return p && p->cache_valid ? p->cache_token : 0; }
 
 int paths_free(pt_paths* p) {
     if (!p) return PT_OK;
@@ -687,7 +723,7 @@ int loss_residual(const double* images, const double* gt, int64_t n, double* dld
     cudaStream_t st = S_(stream);
     if (loss) PT_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), st));
     if (n == 0) return PT_OK;
-    k_resid<<<grid_for(n, 256, 152 * 4), 256, 0, st>>>(images, gt, n, dldi, loss);
+    k_resid<<<grid_for(n, 256, 4), 256, 0, st>>>(images, gt, n, dldi, loss);
     return launch_status("loss_residual");
 }
 
@@ -716,12 +752,7 @@ struct pt_batch {
 };
 
 namespace {
-int sm_count() {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return std::max(1, sms);
-}
+int sm_count() { return device_sms(); }
 
 int ensure_cache(pt_paths* p, cudaStream_t st) {
     const uint64_t need = p->ev.cap * (uint64_t)p->scene->ds.n_cams;
@@ -842,7 +873,7 @@ int batch_reweight(pt_batch* b, uint32_t flags, void* stream) {
         for (const GroupTable& t : b->groups) launch_group_reweight(t, (flags & PT_CACHE) != 0, b->reg_cap, st);
     else
         launch_batch_reweight(b->dev, n, b->q, (flags & PT_CACHE) != 0, b->reg_cap, b->blocks, st);
-    for (int s = 0; s < n; ++s) b->paths[s]->cache_valid = (flags & PT_CACHE) != 0;
+    for (int s = 0; s < n; ++s) set_cache(b->paths[s], (flags & PT_CACHE) != 0, b->host[s].beta_t);
     return launch_status("batch_reweight");
 }
 

@@ -186,6 +186,7 @@ void launch_grad_reference(const DevScene& S, const SortedPaths& P, const float*
 // return `code`; validate a scene description and derive its constants
 // (hc: n_cams cameras, tans: 2 * n_cams half-field tangents x, y)
 int fail(int code, const char* fmt, ...);
+int device_sms();                               // SMs of the current device (cached per device)
 const DevCam* scene_cams(const pt_scene* sc);   // device camera table of a scene
 const float* scene_omega(const pt_scene* sc);   // device pixel solid angles of a scene
 int describe_scene(const pt_scene_desc* d, DevScene& S, DevCam* hc, double* tans);

@@ -244,7 +244,7 @@ void launch_grad_reference(const DevScene& S, const SortedPaths& P, const float*
 
 void launch_delta(const float* a, const float* b, float* out, int64_t n, cudaStream_t st) {
     const int bs = 256;
-    unsigned g = (unsigned)std::min<int64_t>((n + bs - 1) / bs, 152 * 16);
+    unsigned g = (unsigned)std::min<int64_t>((n + bs - 1) / bs, (int64_t)device_sms() * 16);
     if (g == 0) return;
     k_delta<<<g, bs, 0, st>>>(a, b, out, n);
 }

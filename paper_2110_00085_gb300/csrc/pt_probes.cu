@@ -62,6 +62,37 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(void* __restrict__ buf,
     if (KIND == PT_PROBE_GATHER_F32) sink[tid] = acc;
 }
 
+// shared-memory atomics (the accumulation a block could do before its
+// FP64 reductions leave the SM): a table of 16 KB per block
+template <int KIND>
+__global__ void __launch_bounds__(kProbeThreads) k_probe_shared(float* __restrict__ out, int64_t iters) {
+    constexpr int kSlots = KIND == PT_PROBE_SHARED_F64 ? 2048 : 4096;
+    __shared__ __align__(16) unsigned char tab_raw[16384];
+    float* tf = reinterpret_cast<float*>(tab_raw);
+    uint32_t* tu = reinterpret_cast<uint32_t*>(tab_raw);
+    double* td = reinterpret_cast<double*>(tab_raw);
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) tu[i] = 0u;
+    __syncthreads();
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    // RUN4: the four lanes of a group draw the same sequence
+    uint32_t x = mix(KIND == PT_PROBE_SHARED_F32_RUN4 ? (tid >> 2) : tid);
+    for (int64_t it = 0; it < iters; it += kUnroll) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            x = lcg(x);
+            const uint32_t r = (x >> 20) & (uint32_t)(kSlots - 1);
+            if (KIND == PT_PROBE_SHARED_F32 || KIND == PT_PROBE_SHARED_F32_RUN4)
+                atomicAdd(tf + r, 1.0f);
+            else if (KIND == PT_PROBE_SHARED_U32)
+                atomicAdd(tu + r, 1u);
+            else
+                atomicAdd(td + r, 1.0);
+        }
+    }
+    __syncthreads();
+    out[tid] = tf[threadIdx.x];
+}
+
 __global__ void __launch_bounds__(kProbeThreads) k_probe_copy(float4* __restrict__ dst,
                                                               const float4* __restrict__ src, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -76,7 +107,21 @@ extern "C" int pt_probe(int kind, void* buf, int64_t n, const void* src, int64_t
     if (!buf || n < 1) return pt::fail(PT_E_INVALID, "pt_probe: null buffer or empty size");
     if (blocks < 1 || blocks > (1 << 20)) return pt::fail(PT_E_INVALID, "pt_probe: blocks must be in 1..2^20");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (kind == PT_PROBE_COPY) {
+    if (kind >= PT_PROBE_SHARED_F32) {
+        if (n < (int64_t)blocks * kProbeThreads)
+            return pt::fail(PT_E_INVALID, "pt_probe: shared probes need blocks * 256 output floats");
+        if (iters < 1 || iters > (1 << 24)) return pt::fail(PT_E_INVALID, "pt_probe: iters must be in 1..2^24");
+        const int64_t it = (iters + kUnroll - 1) / kUnroll * kUnroll;
+        float* o = static_cast<float*>(buf);
+        switch (kind) {
+            case PT_PROBE_SHARED_F32: k_probe_shared<PT_PROBE_SHARED_F32><<<blocks, kProbeThreads, 0, st>>>(o, it); break;
+            case PT_PROBE_SHARED_F32_RUN4:
+                k_probe_shared<PT_PROBE_SHARED_F32_RUN4><<<blocks, kProbeThreads, 0, st>>>(o, it);
+                break;
+            case PT_PROBE_SHARED_U32: k_probe_shared<PT_PROBE_SHARED_U32><<<blocks, kProbeThreads, 0, st>>>(o, it); break;
+            default: k_probe_shared<PT_PROBE_SHARED_F64><<<blocks, kProbeThreads, 0, st>>>(o, it); break;
+        }
+    } else if (kind == PT_PROBE_COPY) {
         if (!src) return pt::fail(PT_E_INVALID, "pt_probe: copy needs a source");
         k_probe_copy<<<blocks, kProbeThreads, 0, st>>>(static_cast<float4*>(buf), static_cast<const float4*>(src),
                                                        n);

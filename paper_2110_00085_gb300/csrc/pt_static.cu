@@ -123,7 +123,7 @@ extern "C" int render_forward_static(const pt_scene_desc* desc, const float* bet
         cudaError_t e = cudaMemsetAsync(images, 0, sizeof(double) * (size_t)S.n_pixels, st);
         if (e != cudaSuccess) return fail(PT_E_CUDA, "render_forward_static: memset: %s", cudaGetErrorString(e));
     }
-    const unsigned blocks = (unsigned)std::min<int64_t>((S.n_pixels + 255) / 256, 152 * 8);
+    const unsigned blocks = (unsigned)std::min<int64_t>((S.n_pixels + 255) / 256, (int64_t)device_sms() * 8);
     k_static_setup<<<blocks, 256, 0, st>>>(pack, scr, S.n_pixels);
     S.cams = reinterpret_cast<const DevCam*>(scr);
     S.err = reinterpret_cast<int*>(scr + kOffErr);

@@ -392,7 +392,7 @@ struct pt_surf_paths {
 };
 
 namespace {
-unsigned surf_grid(uint64_t n) { return (unsigned)std::min<uint64_t>((n + 255) / 256, 152 * 16); }
+unsigned surf_grid(uint64_t n) { return (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)device_sms() * 16); }
 
 void free_store(pt_surf_paths* p) {
     cudaFree(p->st.ev); cudaFree(p->st.raw); cudaFree(p->st.bins); cudaFree(p->st.pc); cudaFree(p->st.count);

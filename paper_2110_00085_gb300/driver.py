@@ -208,21 +208,27 @@ class Reconstruction:
         self.epoch = snap["epoch"]
 
     def save(self, path: str):
-        """Checkpoint to a file: the snapshot plus the settings that define the
-        path sets (path budget, N_r, seed, estimator)."""
+        """Checkpoint to a file: the snapshot, the voxel mask (the carved hull,
+        or None) and the settings that define the path sets and the steps
+        (path budget, N_r, seed, estimator, step size)."""
         snap = {k: (v.cpu() if torch.is_tensor(v) else v) for k, v in self.snapshot().items()}
-        snap.update(n_paths=self.n_paths, n_r=self.n_r, seed=self.seed, decorrelate=self.decorrelate)
+        snap.update(n_paths=self.n_paths, n_r=self.n_r, seed=self.seed, decorrelate=self.decorrelate,
+                    lr=float(self.lr), mask=None if self.mask is None else self.mask.to(torch.uint8).cpu())
         torch.save(snap, path)
 
     def load(self, path: str):
         """Resume from save(): exact from a resample boundary (t mod N_r == 0,
         the same paths are drawn again); elsewhere the next step draws paths
-        at the loaded extinction, as its stored paths are not in the file."""
+        at the loaded extinction, as its stored paths are not in the file.
+        The voxel mask is restored; a checkpoint of another path budget, N_r,
+        seed, estimator or step size is refused."""
         snap = torch.load(path, map_location="cpu")
-        for k in ("n_paths", "n_r", "seed", "decorrelate"):
+        for k in ("n_paths", "n_r", "seed", "decorrelate", "lr"):
             if snap[k] != getattr(self, k):
                 raise ValueError(f"checkpoint {k} = {snap[k]} differs from this run's {getattr(self, k)}")
         self.restore(snap)
+        m = snap.get("mask")
+        self.mask = None if m is None else m.to(device=self.beta.device, dtype=torch.uint8).contiguous()
         self._need_store = self.t % self.n_r != 0
 
     def close(self):

@@ -79,6 +79,8 @@ def load():
         L.paths_reweight.argtypes = [_vp, _vp, _vp, _u32, _vp]
         L.render_grad.argtypes = [_vp, _vp, _vp, _vp, _u32, _vp]
         L.paths_free.argtypes = [_vp]
+        L.paths_cache_token.argtypes = [_vp]
+        L.paths_cache_token.restype = _u64
         L.paths_info.argtypes = [_vp, C.POINTER(PtPathsInfo), _vp]
         L.adam_step.argtypes = [_vp, _vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.c_float, C.c_float, C.c_float,
                                 C.c_float, _vp]
@@ -270,6 +272,10 @@ class Paths:
         _check(rc, "render_grad")
         return grad
 
+    def cache_token(self) -> int:
+        """Which cache-writing reweight the contribution cache holds (0: none)."""
+        return int(load().paths_cache_token(self._h))
+
     def info(self, stream=None) -> dict:
         inf = PtPathsInfo()
         _check(load().paths_info(self._h, C.byref(inf), _vp(_stream(stream))), "paths_info")
@@ -373,7 +379,8 @@ def render_forward_static(sc, beta: torch.Tensor, n_paths: int, seed: int, first
     return images
 
 
-PROBE_GATHER_F32, PROBE_RED_F64, PROBE_RED_F64_WARP, PROBE_RED_F64_SAME, PROBE_RED_F32, PROBE_COPY = range(6)
+(PROBE_GATHER_F32, PROBE_RED_F64, PROBE_RED_F64_WARP, PROBE_RED_F64_SAME, PROBE_RED_F32, PROBE_COPY,
+ PROBE_SHARED_F32, PROBE_SHARED_F32_RUN4, PROBE_SHARED_U32, PROBE_SHARED_F64) = range(10)
 
 
 def probe(kind: int, buf: torch.Tensor, iters: int = 0, blocks: int = 0, src: Optional[torch.Tensor] = None,
@@ -384,7 +391,7 @@ def probe(kind: int, buf: torch.Tensor, iters: int = 0, blocks: int = 0, src: Op
     if not isinstance(buf, torch.Tensor) or not buf.is_cuda or not buf.is_contiguous():
         raise TypeError("probe: buf must be a contiguous CUDA tensor")
     esz = 16 if kind == PROBE_COPY else (8 if kind in (PROBE_RED_F64, PROBE_RED_F64_WARP, PROBE_RED_F64_SAME)
-                                          else 4)
+                                          else 4)   # shared probes: one float32 per thread
     n = buf.numel() * buf.element_size() // esz
     sp = None
     if src is not None:

@@ -9,6 +9,8 @@ the paths whose fingerprints differ are rendered one by one on each side
 element-wise comparison.  No value computed by the CUDA path enters the
 oracle: only the list of path ids to leave out is shared.
 """
+import os
+
 import numpy as np
 import torch
 
@@ -18,6 +20,13 @@ from paper_2110_00085_gb300 import native as N
 RTOL = 1e-4          # per pixel, per voxel (of the voxel's absolute term mass)
 MAX_DIVERGENT = 2e-3  # fraction of paths whose discrete decisions may differ
 U32 = 2.0 ** -24      # FP32 unit roundoff
+THREADS = os.cpu_count() or 1   # oracle threads (the split does not change its results)
+# Elements (lit pixels, touched voxels) that pass only through the oracle's
+# measured float32 budget -- their error exceeds RTOL of the value (pixels)
+# or of the term mass (voxels) -- may be at most this fraction of the
+# non-zero elements; every comparison prints its count and the largest
+# budget / (RTOL x value) ratio.
+MAX_BUDGET_ONLY = 5e-3
 
 
 def t32(a):
@@ -40,7 +49,8 @@ def assert_images_close(gi, oi, rtol=RTOL, what="images", cond=None):
     collision in thin air just past cloud edges, a near-tie of the pixel)."""
     gi = np.asarray(gi)
     oi = np.asarray(oi)
-    atol = 1e-9 * max(np.abs(oi).max(), 1e-300)
+    floor = 1e-9 * max(np.abs(oi).max(), 1e-300)
+    atol = floor
     if cond is not None:
         atol = atol + np.asarray(cond)
     err = np.abs(gi - oi)
@@ -50,6 +60,7 @@ def assert_images_close(gi, oi, rtol=RTOL, what="images", cond=None):
         k = np.argmax(err / budget)
         raise AssertionError(f"{what}: {bad.sum()} of {bad.size} elements off; worst at {k}: "
                              f"gpu {gi[k]:.9e} oracle {oi[k]:.9e} budget {np.broadcast_to(budget, oi.shape)[k]:.3e}")
+    _budget_report(what, err, rtol * np.abs(oi) + floor, cond, oi != 0)
 
 
 def assert_grad_close(gg, og, oabs, ocond=None, rtol=RTOL, what="grad"):
@@ -59,7 +70,8 @@ def assert_grad_close(gg, og, oabs, ocond=None, rtol=RTOL, what="grad"):
     paths, plus the roundoff of the crossing times)."""
     gg = np.asarray(gg)
     err = np.abs(gg - og)
-    floor = 1e-12 * max(oabs.max(), 1e-300)
+    floor0 = 1e-12 * max(oabs.max(), 1e-300)
+    floor = floor0
     if ocond is not None:
         floor = floor + ocond
     bad = err > rtol * oabs + floor
@@ -68,6 +80,25 @@ def assert_grad_close(gg, og, oabs, ocond=None, rtol=RTOL, what="grad"):
         k = np.argmax(err / budget)
         raise AssertionError(f"{what}: {bad.sum()} of {bad.size} voxels off; worst at {k}: gpu {gg[k]:.9e} "
                              f"oracle {og[k]:.9e} |terms| {oabs[k]:.3e} budget {budget[k]:.3e}")
+    _budget_report(what, err, rtol * oabs + floor0, ocond, oabs != 0)
+
+
+def _budget_report(what, err, base, cond, nonzero):
+    """Counts the elements whose error exceeds the base tolerance (RTOL of
+    the value or term mass) and that pass only through the float32 budget;
+    prints the count and the largest budget / base ratio, and bounds the
+    count by MAX_BUDGET_ONLY of the non-zero elements."""
+    n = int(np.count_nonzero(nonzero))
+    over = (err > base) & nonzero
+    k = int(np.count_nonzero(over))
+    ratio = 0.0
+    if cond is not None and n:
+        c = np.broadcast_to(np.asarray(cond, dtype=np.float64), err.shape)[nonzero]
+        ratio = float(np.max(c / np.maximum(base[nonzero], 1e-300)))
+    print(f"[parity] {what}: {k} of {n} non-zero elements pass only through the float32 budget "
+          f"({k / max(n, 1):.2e}); largest budget / ({RTOL:g} x value) = {ratio:.3g}")
+    assert k <= MAX_BUDGET_ONLY * n, (f"{what}: {k} of {n} non-zero elements need the float32 budget "
+                                      f"(more than {MAX_BUDGET_ONLY:g})")
 
 
 def forward_parity(sc, beta, n, first=0, seed=None):
@@ -78,8 +109,10 @@ def forward_parity(sc, beta, n, first=0, seed=None):
     fp = torch.zeros(n, dtype=torch.int64, device="cuda")
     tal = torch.zeros(N.TALLY_COUNT, dtype=torch.float64, device="cuda")
     img = scene.render_forward(b, n, seed, first=first, tallies=tal, fingerprints=fp)
-    ref = O.render(sc, beta, first=first, n=n, seed=seed, fingerprints=True, tallies=True, image_cond=True)
+    ref = O.render(sc, beta, first=first, n=n, seed=seed, fingerprints=True, tallies=True, image_cond=True,
+                   threads=THREADS)
     div = divergent(fp, ref["fingerprints"], first)
+    print(f"[parity] forward: {len(div)} of {n} paths divergent ({len(div) / n:.2e})")
     assert len(div) <= max(3, MAX_DIVERGENT * n), f"{len(div)} divergent paths of {n}"
     gi = img.clone()
     oi = ref["images"].copy()
@@ -101,7 +134,7 @@ def recycled_parity(sc, beta_ref, beta_t, n, dldi=None, cache=False, first=0):
     paths = N.Paths(scene).store(br, n, sc.seed, first=first, fingerprints=fp)
     img = paths.reweight(bt, cache=cache)
     ref = O.render(sc, beta_ref, beta_t, first=first, n=n, fingerprints=True, image_cond=True,
-                   dldi=dldi, grad_abs=dldi is not None, grad_cond=dldi is not None)
+                   dldi=dldi, grad_abs=dldi is not None, grad_cond=dldi is not None, threads=THREADS)
     out = {"gpu_images": img, "oracle_images": ref["images"].copy(), "oracle_image_cond": ref["image_cond"]}
     if dldi is not None:
         g = paths.grad(bt, t64(dldi), cache=cache)
@@ -110,6 +143,7 @@ def recycled_parity(sc, beta_ref, beta_t, n, dldi=None, cache=False, first=0):
         out["oracle_grad_abs"] = ref["grad_abs"]
         out["oracle_grad_cond"] = ref["grad_cond"]
     div = divergent(fp, ref["fingerprints"], first)
+    print(f"[parity] recycled: {len(div)} of {n} paths divergent ({len(div) / n:.2e})")
     assert len(div) <= max(3, MAX_DIVERGENT * n), f"{len(div)} divergent paths of {n}"
     for p in div:
         one = N.Paths(scene).store(br, 1, sc.seed, first=int(p), n_norm=n)

@@ -48,6 +48,7 @@ def test_null_arguments_are_rejected_without_a_gpu():
     assert L.adam_step(None, None, None, None, None, 0, 0, 0.0, 0.0, 0.0, 0.0, None) == 1
     assert L.pt_inject_error(None, 1, None) == 1
     assert L.pt_check(None, None) == 1
+    assert L.paths_cache_token(None) == 0
 
 
 def test_scene_descriptor_validation_runs_on_host():

@@ -52,6 +52,40 @@ def test_autograd_backward_matches_oracle():
     assert_grad_close(g, ref["grad"], ref["grad_abs"], ref["grad_cond"] + 2.0 * 2 ** -24 * np.abs(ref["grad"]))
 
 
+def test_two_forwards_then_backward_of_the_first():
+    """A second forward on the same stored paths replaces the contribution
+    cache; the backward of the first must still differentiate the first
+    extinction (its cache token is stale, so it re-traces the shadow rays)
+    and equal a fresh single forward and backward.  The raw call refuses a
+    cached gradient for a grid other than the cached reweight's."""
+    sc, bt, gt = _setup()
+    n = sc.n_paths
+    scene = N.Scene(sc)
+    paths = N.Paths(scene).store(t32(sc.beta_cloud), n, sc.seed)
+    b1 = t32(bt).requires_grad_(True)
+    b2 = t32(bt * 1.1).requires_grad_(True)
+    img1 = AG.render(b1, paths)
+    tok1 = paths.cache_token()
+    img2 = AG.render(b2, paths)
+    assert tok1 != 0 and paths.cache_token() not in (0, tok1)
+    (0.5 * ((img1 - t64(gt)) ** 2).sum()).backward()
+    assert b2.grad is None
+    ref_paths = N.Paths(scene).store(t32(sc.beta_cloud), n, sc.seed)
+    br = t32(bt).requires_grad_(True)
+    img_r = AG.render(br, ref_paths)
+    (0.5 * ((img_r - t64(gt)) ** 2).sum()).backward()
+    torch.cuda.synchronize()
+    assert torch.allclose(img1, img_r, rtol=1e-12, atol=0)
+    assert not torch.allclose(img2, img_r, rtol=1e-3, atol=0)
+    # re-traced vs cached: the same terms summed in another order (FP32
+    # pre-sums of same-voxel terms before the FP64 reductions)
+    assert torch.allclose(b1.grad, br.grad, rtol=1e-5, atol=1e-7 * float(br.grad.abs().max()))
+    with pytest.raises(RuntimeError, match="another extinction grid"):
+        paths.grad(t32(bt * 1.1), t64(gt), cache=True)
+    paths.close()
+    ref_paths.close()
+
+
 def test_autograd_finite_difference_smoke():
     """64^3 blobs in air (two particle types)."""
     sc, bt, gt = _setup(1 << 14, cfg=2)

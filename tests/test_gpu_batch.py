@@ -69,8 +69,9 @@ def test_batch_matches_oracle_and_per_scene_calls():
     paths = [N.Paths(s).store(t32(b), sc.n_paths, sc.seed, fingerprints=f)
              for s, b, sc, f in zip(scenes, br, specs, fps)]
     # per-scene calls on the same stored paths
-    ref_img = [p.reweight(t32(b), cache=True) for p, b in zip(paths, bt)]
-    ref_grad = [p.grad(t32(b), t64(d), cache=True) for p, b, d in zip(paths, bt, dl)]
+    btd = [t32(b) for b in bt]
+    ref_img = [p.reweight(b, cache=True) for p, b in zip(paths, btd)]
+    ref_grad = [p.grad(b, t64(d), cache=True) for p, b, d in zip(paths, btd, dl)]
     # one batched launch per pass over all three scenes
     imgs = [s.new_images() for s in scenes]
     grads = [torch.zeros(s.n_voxels, dtype=torch.float64, device="cuda") for s in scenes]

@@ -59,8 +59,9 @@ def full_run(case):
     ref = scene.new_images()
     p = N.Paths(scene).store(t32(br), FULL, sc.seed, images_ref=ref, tallies=tal, fingerprints=fp)
     same = p.reweight(t32(br), cache=False)
-    img = p.reweight(t32(bt), cache=True)
-    g = p.grad(t32(bt), t64(dl), cache=True)
+    btd = t32(bt)
+    img = p.reweight(btd, cache=True)
+    g = p.grad(btd, t64(dl), cache=True)
     torch.cuda.synchronize()
     scene.check()
     out = {"fp": fp.cpu().numpy().view(np.uint64), "tallies": dict(zip(N.TALLY_NAMES, tal.cpu().numpy())),
@@ -95,14 +96,15 @@ def test_fullsize_sampled_paths_match_oracle_elementwise(case, full_run):
     ocond = np.zeros(scene.n_voxels)
     icond = np.zeros(scene.n_pixels)
     used = 0
+    btd, dld = t32(bt), t64(dl)
     for pid in ids:
         o = O.render(sc, br, bt, first=pid, n=1, n_norm=FULL, dldi=dl, grad_abs=True, grad_cond=True,
                      image_cond=True, fingerprints=True)
         if o["fingerprints"][0] != full_run["fp"][pid]:
             continue    # a near-tie of a discrete decision: compared by neither side
         one = N.Paths(scene).store(t32(br), 1, sc.seed, first=pid, n_norm=FULL)
-        one.reweight(t32(bt), gi, cache=True, accumulate=True)
-        one.grad(t32(bt), t64(dl), gg, cache=True, accumulate=True)
+        one.reweight(btd, gi, cache=True, accumulate=True)
+        one.grad(btd, dld, gg, cache=True, accumulate=True)
         one.close()
         oi += o["images"]; og += o["grad"]; oabs += o["grad_abs"]; ocond += o["grad_cond"]
         icond += o["image_cond"]
@@ -119,10 +121,11 @@ def test_fullsize_launch_equals_two_half_launches(case, full_run):
     half = FULL // 2
     img = scene.new_images()
     g = torch.zeros(scene.n_voxels, dtype=torch.float64, device="cuda")
+    btd, dld = t32(bt), t64(dl)
     for first in (0, half):
         p = N.Paths(scene).store(t32(br), half, sc.seed, first=first, n_norm=FULL)
-        p.reweight(t32(bt), img, cache=True, accumulate=True)
-        p.grad(t32(bt), t64(dl), g, cache=True, accumulate=True)
+        p.reweight(btd, img, cache=True, accumulate=True)
+        p.grad(btd, dld, g, cache=True, accumulate=True)
         torch.cuda.synchronize()
         p.close()
     scene.check()
@@ -171,8 +174,9 @@ def test_batch_fullsize_matches_per_scene_calls_and_oracle_fingerprints():
     for s, sc, b, bb, d in zip(scenes, specs, br, bt, dl):
         fp = torch.zeros(sc.n_paths, dtype=torch.int64, device="cuda")
         p = N.Paths(s).store(t32(b), sc.n_paths, sc.seed, fingerprints=fp)
-        ref_img.append(p.reweight(t32(bb), cache=True).cpu().numpy())
-        ref_g.append(p.grad(t32(bb), t64(d), cache=True).cpu().numpy())
+        bbd = t32(bb)
+        ref_img.append(p.reweight(bbd, cache=True).cpu().numpy())
+        ref_g.append(p.grad(bbd, t64(d), cache=True).cpu().numpy())
         fps.append(fp.cpu().numpy().view(np.uint64))
         paths.append(p)
     imgs = [s.new_images() for s in scenes]
@@ -222,8 +226,9 @@ def test_cumulus256_chunked_fullsize():
     cp.store(t32(br), n, sc.seed, images_ref=ref, tallies=tal, fingerprints=fp)
     assert len(cp.parts) == 4
     same = cp.reweight(t32(br), cache=False)
-    img = cp.reweight(t32(bt), cache=True)
-    g = cp.grad(t32(bt), t64(dl), cache=True)
+    btd = t32(bt)
+    img = cp.reweight(btd, cache=True)
+    g = cp.grad(btd, t64(dl), cache=True)
     torch.cuda.synchronize()
     scene.check()
     info = cp.info()
@@ -256,8 +261,8 @@ def test_cumulus256_chunked_fullsize():
         if o["fingerprints"][0] != fph[pid]:
             continue
         one = N.Paths(scene).store(t32(br), 1, sc.seed, first=pid, n_norm=n)
-        one.reweight(t32(bt), gi, cache=True, accumulate=True)
-        one.grad(t32(bt), t64(dl), gg, cache=True, accumulate=True)
+        one.reweight(btd, gi, cache=True, accumulate=True)
+        one.grad(btd, dld, gg, cache=True, accumulate=True)
         one.close()
         oi += o["images"]; icond += o["image_cond"]
         og += o["grad"]; oabs += o["grad_abs"]; ocond += o["grad_cond"]

@@ -11,7 +11,8 @@ import oracle as O
 from paper_2110_00085_gb300 import native as N
 from paper_2110_00085_gb300 import synth
 
-from _parity import (RTOL, assert_grad_close, assert_images_close, forward_parity, recycled_parity, t32, t64)
+from _parity import (RTOL, THREADS, assert_grad_close, assert_images_close, forward_parity, recycled_parity, t32,
+                     t64)
 
 pytestmark = pytest.mark.gpu
 
@@ -125,6 +126,25 @@ def test_gradient_matches_oracle(cfg, n, cache):
     out = recycled_parity(sc, sc.beta_cloud, bt, n, dldi=dldi, cache=cache)
     assert np.abs(out["oracle_grad"]).max() > 0
     assert_grad_close(out["gpu_grad"], out["oracle_grad"], out["oracle_grad_abs"], out["oracle_grad_cond"])
+
+
+def test_noise128_consecutive_paths_match_oracle_elementwise():
+    """The timed workload's grid and cameras (128^3 thresholded noise, 15
+    cameras of 128x128): one store of 2^14 consecutive paths, cached
+    reweight and cached gradient as in the timed step, compared element by
+    element -- the gradient kernel's warps sum same-voxel terms of different
+    paths' events (lateral ray order, run merge) before their FP64 adds."""
+    n = 1 << 14
+    sc = synth.config(3, n_paths=n)
+    bt = _perturbed(sc.beta_cloud, seed=33, lo=0.9, hi=1.1)
+    gt = 0.8 * O.render(sc, sc.beta_cloud, n=n, seed=sc.seed + 99, threads=THREADS)["images"]
+    F = O.render(sc, sc.beta_cloud, bt, n=n, threads=THREADS)["images"]
+    out = recycled_parity(sc, sc.beta_cloud, bt, n, dldi=F - gt, cache=True)
+    assert np.abs(out["oracle_images"]).max() > 0 and np.abs(out["oracle_grad"]).max() > 0
+    assert_images_close(out["gpu_images"], out["oracle_images"], what="noise128 images",
+                        cond=out["oracle_image_cond"])
+    assert_grad_close(out["gpu_grad"], out["oracle_grad"], out["oracle_grad_abs"], out["oracle_grad_cond"],
+                      what="noise128 gradient")
 
 
 def test_gradient_cache_equals_recompute():

@@ -162,6 +162,8 @@ def test_reconstruction_resumes_from_a_file_checkpoint(tmp_path):
     bt = torch.from_numpy(sc.beta_cloud.reshape(-1).astype(np.float32)).cuda()
     gt = scene.render_forward(bt, 1 << 15, 999)
     rec = Reconstruction(scene, gt, bt * 0.8, 1 << 14, n_r=3, lr=0.1, seed=5, decorrelate=True)
+    # a carved hull: half of the voxels are not optimised
+    rec.mask = (torch.arange(scene.n_voxels, device="cuda") % 2).to(torch.uint8)
     for _ in range(3):
         rec.step()
     f = str(tmp_path / "ckpt.pt")
@@ -173,10 +175,16 @@ def test_reconstruction_resumes_from_a_file_checkpoint(tmp_path):
     rec.close()
     other = Reconstruction(scene, gt, bt * 0.5, 1 << 14, n_r=3, lr=0.1, seed=5, decorrelate=True)
     other.load(f)
+    assert other.mask is not None and torch.equal(other.mask, rec.mask)
     for _ in range(4):
         other.step()
     torch.cuda.synchronize()
     assert torch.allclose(other.beta, a, rtol=1e-5, atol=1e-6)
+    # masked voxels kept the loaded extinction
+    keep = rec.mask == 0
+    assert torch.equal(other.beta[keep], (bt * 0.8)[keep])
     other.close()
     with pytest.raises(ValueError, match="seed"):
         Reconstruction(scene, gt, bt, 1 << 14, n_r=3, lr=0.1, seed=6, decorrelate=True).load(f)
+    with pytest.raises(ValueError, match="lr"):
+        Reconstruction(scene, gt, bt, 1 << 14, n_r=3, lr=0.2, seed=5, decorrelate=True).load(f)

@@ -47,6 +47,27 @@ def test_static_entry_matches_scene_entry_on_two_calls():
         assert_images_close(got.cpu().numpy(), ref.cpu().numpy(), rtol=RTOL, what="static entry images")
 
 
+def test_static_entry_allocates_no_device_memory():
+    """The property the entry point exists for: after the first call on the
+    device (which looks up the array's address and loads the kernel),
+    repeated calls into a caller-owned image buffer leave the device's free
+    memory and torch's reserved memory unchanged."""
+    sc = synth.config(1, n_paths=1 << 12)
+    b = t32(sc.beta_cloud)
+    img = torch.zeros(sc.n_pixels, dtype=torch.float64, device=b.device)
+    first = N.render_forward_static(sc, b, sc.n_paths, 3, images=img)
+    assert first.data_ptr() == img.data_ptr()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    reserved0 = torch.cuda.memory_reserved()
+    for k in range(5):
+        N.render_forward_static(sc, b, sc.n_paths, 4 + k, images=img)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_reserved() == reserved0
+    assert img.abs().max().item() > 0
+
+
 def test_static_entry_rejects_scenes_over_its_limits():
     sc = synth.config(1, n_paths=16)
     b = t32(sc.beta_cloud)
