@@ -155,10 +155,23 @@ def oracle_sample(sc, beta, target_s: float, threads: int):
     return n / dt, n, dt
 
 
-def workload(n_paths=None):
+# single-scene workloads: name -> (synth.config number, description)
+CONFIGS = {
+    "noise128": (3, WORKLOAD),
+    "blobs32": (1, "blobs32: 32^3 grid of 3 Gaussian blobs (peak 20/km, 20 m voxels), 9 cameras 32x32 on a 60 deg "
+                   "arc, sun 30 deg, 2^18 stored paths recycled for N_r=10 Adam steps, 10 orders, roulette after 5"),
+    "blobs64_air": (2, "blobs64_air: 64^3 grid of 8 Gaussian blobs (peak 20/km) in air 0.01/km (albedo 1, "
+                       "Rayleigh), 9 cameras 64x64, 2^22 stored paths recycled for N_r=10 Adam steps"),
+    "cumulus256_air": (5, "cumulus256_air: 256^3 5-octave fractal cumulus (max 80/km, 10 m voxels) in air "
+                          "0.01/km, 21 cameras 256x256, 2^28 paths per resample (4 stored chunks of 2^26), "
+                          "recycled for N_r=10 Adam steps"),
+}
+
+
+def workload(n_paths=None, name="noise128"):
     import numpy as np
     from paper_2110_00085_gb300 import synth
-    sc = synth.config(3)
+    sc = synth.config(CONFIGS[name][0])
     if n_paths:
         sc = sc.replace(n_paths=int(n_paths))
     gt = sc.beta_cloud
@@ -169,7 +182,8 @@ def workload(n_paths=None):
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    sc, gt, beta0 = workload(args.paths)
+    name = args.workload if args.workload in CONFIGS else "noise128"
+    sc, gt, beta0 = workload(args.paths, name)
     threads = os.cpu_count() or 1
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
@@ -186,7 +200,7 @@ def run_reference(args, ws, rank):
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * sc.n_paths / value, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n_paths": sc.n_paths, "n_r": N_R,
+           "config": {"workload": CONFIGS[name][1], "n_paths": sc.n_paths, "n_r": N_R,
                       "note": "ms_per_step extrapolated from the sample rate to the full path budget"},
            "cpu_baseline": cb,
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -454,7 +468,7 @@ def calibrate_matched(args, ws, scene, gt_img, beta0, n, lr, seed, reuse_ms):
     return out
 
 
-def ablation(args, ws, scene, gt_img, beta_gt, beta0, n, lr, seed, steps=50):
+def ablation(args, ws, scene, gt_img, beta_gt, beta0, n, lr, seed, steps=50, decorrelate=False):
     """Norm-free comparison of Alg. 2 (N_r = 10) and Alg. 1 (N_r = 1), the
     volume analogue of the paper's recycling ablation (Sec. 6): the same
     start, path budget and step size, ``steps`` Adam steps each; per step
@@ -466,7 +480,7 @@ def ablation(args, ws, scene, gt_img, beta_gt, beta0, n, lr, seed, steps=50):
     gsum = float(beta_gt.double().sum())
     arms = {}
     for n_r in (N_R, 1):
-        rec = Reconstruction(scene, gt_img, beta0, n, n_r=n_r, lr=lr, seed=seed, cache=True)
+        rec = Reconstruction(scene, gt_img, beta0, n, n_r=n_r, lr=lr, seed=seed, cache=True, decorrelate=decorrelate)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
         loss = torch.zeros(steps, dtype=torch.float64, device=beta0.device)
         eps = torch.zeros(steps, dtype=torch.float64, device=beta0.device)
@@ -489,21 +503,61 @@ def ablation(args, ws, scene, gt_img, beta_gt, beta0, n, lr, seed, steps=50):
                               "eps": [float(f"{x:.4g}") for x in eps.cpu().tolist()]}
     a, b = arms[f"n_r={N_R}"], arms["n_r=1"]
 
-    def first_time(arm, key, level):
-        for t, v in zip(arm["t_s"], arm[key]):
-            if v <= level:
-                return t
-        return None
-
+    # the loss of freshly drawn paths: every step of Alg. 1, the resample
+    # steps (t mod N_r == 0, where r == 1) of Alg. 2; the loss of a reused
+    # path set is not comparable (Adam fits that set's noise within a window)
+    for arm, every in ((a, N_R), (b, 1)):
+        arm["loss_fresh"] = {"step": list(range(0, steps, every)), "t_s": arm["t_s"][::every],
+                             "loss": arm["loss"][::every]}
     summary = {}
-    for key in ("eps", "loss"):
-        level = max(min(a[key]), min(b[key]))   # a level both arms reach
-        ta, tb = first_time(a, key, level), first_time(b, key, level)
+    for key in ("eps", "loss_fresh"):
+        sa = a["loss_fresh"]["loss"] if key == "loss_fresh" else a[key]
+        sb = b["loss_fresh"]["loss"] if key == "loss_fresh" else b[key]
+        ta_s = a["loss_fresh"]["t_s"] if key == "loss_fresh" else a["t_s"]
+        tb_s = b["loss_fresh"]["t_s"] if key == "loss_fresh" else b["t_s"]
+        level = max(min(sa), min(sb))   # a level both arms reach
+        ta = next((t for t, v in zip(ta_s, sa) if v <= level), None)
+        tb = next((t for t, v in zip(tb_s, sb) if v <= level), None)
         summary[key] = {"level_both_reach": level, f"t_s_n_r={N_R}": ta, "t_s_n_r=1": tb,
                         "speedup_reuse": (tb / ta) if ta and tb else None,
-                        f"final_n_r={N_R}": a[key][-1], "final_n_r=1": b[key][-1]}
-    return {"steps": steps, "lr": lr, "n_paths": n, "start": "uniform mean of the true field (reading R11)",
-            "arms": arms, "summary": summary}
+                        f"final_n_r={N_R}": sa[-1], "final_n_r=1": sb[-1]}
+    same = a["loss"]
+    summary["reused_set_loss"] = {"first_in_window": same[0], "last_in_window": same[N_R - 1],
+                                  "note": "the loss on the stored set falls within each window while the "
+                                          "fresh-path loss at the next resample does not (overfitting the set)"}
+    return {"steps": steps, "lr": lr, "n_paths": n, "decorrelate": decorrelate,
+            "start": "uniform mean of the true field (reading R11)", "arms": arms, "summary": summary}
+
+
+def run_ablation(args, ws, rank, local):
+    """The recycling ablation over step sizes and both gradient estimators
+    (the paper's same-set one and the decorrelated one) on a single-scene
+    workload (--ablation-config, default noise128; --paths overrides its
+    budget); one JSON line with every run's trajectories and summary."""
+    import torch
+    import __graft_entry__ as G
+    G.build()
+    from paper_2110_00085_gb300 import native as N
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    name = args.ablation_config
+    sc, gt_np, beta0_np = workload(args.paths, name)
+    n = sc.n_paths
+    scene = N.Scene(sc, scene_id=rank)
+    beta_gt = torch.from_numpy(gt_np.reshape(-1)).to(dev)
+    beta0 = torch.from_numpy(beta0_np.reshape(-1)).to(dev)
+    gt_img = scene.new_images()
+    for k in range(4):
+        scene.render_forward(beta_gt, n, sc.seed + 7919, first=k * n, n_norm=4 * n, images=gt_img, accumulate=True)
+    runs = []
+    for div in [float(x) for x in args.ablation_lr_div.split(",")]:
+        for dec in (False, True):
+            r = ablation(args, ws, scene, gt_img, beta_gt, beta0, n, float(gt_np.max()) / div, sc.seed + rank,
+                         steps=args.ablation_steps, decorrelate=dec)
+            r["lr_rule"] = f"max/{div:g}"
+            runs.append(r)
+    if rank == 0:
+        print(json.dumps({"workload": CONFIGS[name][1], "n_paths": n, "ablation_runs": runs}), flush=True)
 
 
 def run_recon(args, ws, rank, local):
@@ -783,15 +837,19 @@ def run_native(args, ws, rank, local):
     dev = torch.device("cuda", local)
     # the memory rates the passes are bounded by, measured on this device
     probes = measure_peaks(dev)
-    sc, gt_np, beta0_np = workload(args.paths)
+    sc, gt_np, beta0_np = workload(args.paths, args.workload)
     n = sc.n_paths
     scene = N.Scene(sc, scene_id=rank)
     beta_gt = torch.from_numpy(gt_np.reshape(-1)).to(dev)
     beta0 = torch.from_numpy(beta0_np.reshape(-1)).to(dev)
-    # ground-truth images: independent seed, 4x the path budget (not timed)
+    # ground-truth images: independent seed, 4x the path budget (not timed;
+    # 1x above 2^26 paths), in chunks of at most 2^26 paths
     gt_img = scene.new_images()
-    for k in range(4):
-        scene.render_forward(beta_gt, n, sc.seed + 7919, first=k * n, n_norm=4 * n, images=gt_img, accumulate=True)
+    gt_n = 4 * n if n <= (1 << 26) else n
+    step_n = min(n, 1 << 26)
+    for first in range(0, gt_n, step_n):
+        scene.render_forward(beta_gt, min(step_n, gt_n - first), sc.seed + 7919, first=first, n_norm=gt_n,
+                             images=gt_img, accumulate=True)
     lr = float(gt_np.max()) / 50.0
 
     def make(n_r):
@@ -854,8 +912,11 @@ def run_native(args, ws, rank, local):
     res.paths.close()
 
     # ---- matched gradient error: reuse at n vs resample at n* ----
+    # (above 2^26 paths the reference gradients of 4N paths and the
+    # ablation's 2 x 50 steps take too long for one run: not measured there)
+    heavy = not args.no_calibration and n <= (1 << 26)
     matched = None
-    if not args.no_calibration:
+    if heavy:
         matched = calibrate_matched(args, ws, scene, gt_img, beta0, n, lr, sc.seed + rank, ms)
 
     # ---- end to end through the public API with host buffers ----
@@ -883,12 +944,18 @@ def run_native(args, ws, rank, local):
     # ---- rooflines: L2 (the dominant bound), HBM and ALU views per call ----
     avg = {k: sum(v) / len(v) for k, v in kern.items() if v}
     tot = {k: sum(v) for k, v in kern.items()}
+    # one store per N_r steps, from the per-call means (the residual and Adam
+    # share of the timed steps added in): the step time of a long run, also
+    # for K that is not a multiple of N_r
+    other = (ms * args.steps - sum(tot.values())) / args.steps
+    amortized = (avg.get("paths_store", 0.0) / N_R + avg.get("paths_reweight", 0.0) + avg.get("render_grad", 0.0)
+                 + max(other, 0.0))
     dom = max(tot, key=tot.get)
     roof = rooflines(avg, dom, T, info, n, len(sc.cameras), probes, dev)
 
     # ---- the recycling ablation (norm-free): Alg. 2 vs Alg. 1 in time ----
     abl = None
-    if not args.no_calibration:
+    if heavy:
         abl = ablation(args, ws, scene, gt_img, beta_gt, beta0, n, lr, sc.seed + rank, steps=args.ablation_steps)
 
     cpu = None
@@ -904,7 +971,7 @@ def run_native(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_paths": n, "n_r": N_R, "replicas": ws,
+        "config": {"workload": CONFIGS[args.workload][1], "n_paths": n, "n_r": N_R, "replicas": ws,
                    "accumulation": "f64 pixel and gradient sums",
                    "l2": "inputs larger than L2 (stored paths and contribution cache, GBs per step)",
                    "stored_paths": int(info["n_stored"]), "records": int(info["n_records"]),
@@ -914,6 +981,7 @@ def run_native(args, ws, rank, local):
         "matched_error": matched,
         "ablation": abl,
         "kernels_ms": {k: round(v, 3) for k, v in avg.items()},
+        "amortized_ms_per_step": amortized,
         "roofline": roof["main"],
         "roofline_views": roof["views"],
         "peaks": probes,
@@ -939,7 +1007,12 @@ def main():
     ap.add_argument("--no-calibration", action="store_true",
                     help="skip the matched-gradient-error arm and the recycling ablation")
     ap.add_argument("--ablation-steps", type=int, default=50, help="Adam steps per arm of the recycling ablation")
-    ap.add_argument("--workload", default="noise128", choices=["noise128", "batch", "recon", "surfaces", "peaks"])
+    ap.add_argument("--ablation-config", default="noise128", choices=list(CONFIGS),
+                    help="ablation workload: the scene whose ablation runs")
+    ap.add_argument("--ablation-lr-div", default="50,200,800",
+                    help="ablation workload: step sizes as max extinction / these divisors")
+    ap.add_argument("--workload", default="noise128",
+                    choices=list(CONFIGS) + ["batch", "recon", "surfaces", "peaks", "ablation"])
     ap.add_argument("--surf-steps", type=int, default=800, help="surfaces workload: Adam steps per arm")
     ap.add_argument("--path-scale", type=int, default=0, help="batch workload: lower every 2^k path budget by k")
     args = ap.parse_args()
@@ -954,6 +1027,8 @@ def main():
         run_surfaces(args, ws, rank, local)
     elif args.workload == "peaks":
         run_peaks(args, ws, rank, local)
+    elif args.workload == "ablation":
+        run_ablation(args, ws, rank, local)
     else:
         run_native(args, ws, rank, local)
     if ws > 1:

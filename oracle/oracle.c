@@ -689,27 +689,38 @@ static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double
  * sub-path.  Events with zero contribution are skipped (their score may be
  * infinite where beta_c = 0 and there is no air).
  */
-/* float32 error budget of an interval's length: a float32 traversal
- * computes each crossing time t with an error of a few units of roundoff of
- * t itself (budget only, not part of the method) */
-static double time_roundoff(const ivl* iv)
+/* float32 error budget of an interval's length (budget only, not part of
+ * the method): a float32 traversal computes each crossing time t with an
+ * error of a few units of roundoff of t itself, and the face it crosses
+ * sits at a float32 coordinate X, off by up to u |X|, which moves the
+ * crossing time by u |X| / |d_a| (large for a ray nearly parallel to the
+ * face, where the face's coordinate is large against the distance to it) */
+static double face_roundoff(const double p[3], const double d[3], double t, int a)
 {
-    return 4.0 * OR_U32 * (fabs(iv->t0) + fabs(iv->t1));
+    if (a < 0 || d[a] == 0.0) return 0.0;
+    return 2.0 * OR_U32 * fabs(p[a] + t * d[a]) / fabs(d[a]);
+}
+
+static double time_roundoff(const ivl* iv, const double p[3], const double d[3])
+{
+    return 4.0 * OR_U32 * (fabs(iv->t0) + fabs(iv->t1)) + face_roundoff(p, d, iv->t0, iv->a0) +
+           face_roundoff(p, d, iv->t1, iv->a1);
 }
 
 /* the same for an optical depth: sum_i x_i (t1 - t0) with x_i the total
  * extinction under ba (minus that under bb when given); each face trades the
  * jump of x there over its crossing time's roundoff */
-static double depth_roundoff(const or_scene* s, const float* ba, const float* bb, const ivl* iv, int n)
+static double depth_roundoff(const or_scene* s, const float* ba, const float* bb, const ivl* iv, int n,
+                             const double p[3], const double d[3])
 {
     double prev = 0.0, own = 0.0;
     for (int i = 0; i < n; ++i) {
         double x = beta_tot(s, ba, iv[i].v) - (bb ? beta_tot(s, bb, iv[i].v) : 0.0);
-        own += fabs(x - prev) * fabs(iv[i].t0);
+        own += fabs(x - prev) * (4.0 * OR_U32 * fabs(iv[i].t0) + face_roundoff(p, d, iv[i].t0, iv[i].a0));
         prev = x;
     }
-    if (n > 0) own += fabs(prev) * fabs(iv[n - 1].t1);
-    return 4.0 * OR_U32 * own;
+    if (n > 0) own += fabs(prev) * (4.0 * OR_U32 * fabs(iv[n - 1].t1) + face_roundoff(p, d, iv[n - 1].t1, iv[n - 1].a1));
+    return own;
 }
 
 static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
@@ -734,7 +745,7 @@ static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
         int n = intervals(s, P->x[b - 1], P->om[b - 1], P->l[b], c->iv, c->tb);
         log_tr += optical_depth(s, br, c->iv, n) - optical_depth(s, bt, c->iv, n);
         if (icond && br != bt)
-            tr_cond += depth_roundoff(s, br, bt, c->iv, n);
+            tr_cond += depth_roundoff(s, br, bt, c->iv, n, P->x[b - 1], P->om[b - 1]);
         if (b >= 2) {
             int64_t vk = P->v[b - 1];
             double mu = dot3(P->om[b - 2], P->om[b - 1]);
@@ -779,7 +790,7 @@ static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
             if (eval) eval[(b - 1) * s->n_cams + d] = ev * inv_norm;
             /* the shadow ray's and the flights' own float32 crossing times;
              * the vertices' roundoff is measured by perturbation (or_render) */
-            if (icond) icond[gp] += fabs(ev * inv_norm) * (depth_roundoff(s, bt, NULL, c->iv2, ns) + tr_cond);
+            if (icond) icond[gp] += fabs(ev * inv_norm) * (depth_roundoff(s, bt, NULL, c->iv2, ns, P->x[b], dir) + tr_cond);
             if (!dldi || ev == 0.0) continue;
             double A = dldi[gp] * ev * inv_norm;
             /* flights 1..b */
@@ -789,7 +800,7 @@ static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
                     double t = A * (c->iv[i].t1 - c->iv[i].t0);
                     grad_add(c, grad, c->iv[i].v, -t);
                     if (gabs) gabs[c->iv[i].v] += fabs(t);
-                    if (gcond) gcond[c->iv[i].v] += fabs(A) * time_roundoff(&c->iv[i]);
+                    if (gcond) gcond[c->iv[i].v] += fabs(A) * time_roundoff(&c->iv[i], P->x[j - 1], P->om[j - 1]);
                 }
             }
             /* shadow ray x_b -> camera */
@@ -797,7 +808,7 @@ static void eval_path(octx* c, const float* br, const float* bt, const opath* P,
                 double t = A * (c->iv2[i].t1 - c->iv2[i].t0);
                 grad_add(c, grad, c->iv2[i].v, -t);
                 if (gabs) gabs[c->iv2[i].v] += fabs(t);
-                if (gcond) gcond[c->iv2[i].v] += fabs(A) * time_roundoff(&c->iv2[i]);
+                if (gcond) gcond[c->iv2[i].v] += fabs(A) * time_roundoff(&c->iv2[i], P->x[b], dir);
             }
             /* scattering vertices 1..b-1 (angle between sampled directions) */
             for (int j = 1; j < b; ++j) {

@@ -136,11 +136,18 @@ def resample_errors_both(scene: N.Scene, gt: torch.Tensor, betas: Sequence[torch
 
 
 def rel_errors(g: torch.Tensor, g_ref: torch.Tensor) -> Dict[str, float]:
-    """||g - g_ref|| / ||g_ref|| in L2 and in L1."""
+    """||g - g_ref|| / ||g_ref|| in L2 and in L1, with ||g|| / ||g_ref|| and
+    the cosine of the angle between g and g_ref (an estimate that has
+    collapsed toward 0 has error near 1 and a small norm ratio)."""
     d = (g - g_ref).double()
     r = g_ref.double()
-    return {"l2": math.sqrt(float(torch.dot(d, d)) / max(float(torch.dot(r, r)), 1e-300)),
-            "l1": float(d.abs().sum()) / max(float(r.abs().sum()), 1e-300)}
+    gd = g.double()
+    rr = max(float(torch.dot(r, r)), 1e-300)
+    gg = float(torch.dot(gd, gd))
+    return {"l2": math.sqrt(float(torch.dot(d, d)) / rr),
+            "l1": float(d.abs().sum()) / max(float(r.abs().sum()), 1e-300),
+            "norm_ratio": math.sqrt(gg / rr),
+            "cos": float(torch.dot(gd, r)) / math.sqrt(max(gg * rr, 1e-300))}
 
 
 def tail_share(g: torch.Tensor, g_ref: torch.Tensor, frac: float = 1e-3) -> float:
@@ -201,28 +208,36 @@ def matched_errors(rec, n_fresh: Sequence[int], ages: Sequence[int], copies: int
     img = scene.new_images()
     dldi = torch.zeros_like(img)
     gf = torch.zeros(scene.n_voxels, dtype=torch.float64, device=img.device)
-    reuse = {"l2": [], "l1": [], "tail": []}
-    fresh = {int(m): {"l2": [], "l1": [], "tail": []} for m in n_fresh}
+    keys = ("l2", "l1", "norm_ratio", "cos")
+    reuse = {k: [] for k in keys + ("tail",)}
+    fresh = {int(m): {k: [] for k in keys + ("tail",)} for m in n_fresh}
     refnorm = []
     for j, (k, b, g) in enumerate(kept):
         g_ref = reference_gradient(scene, rec.gt, b, rec.n_paths, copies, factor, seed + 1000 * j, epoch=j)
         refnorm.append(float(g_ref.double().norm()))
         e = rel_errors(g, g_ref)
-        reuse["l2"].append(e["l2"]); reuse["l1"].append(e["l1"]); reuse["tail"].append(tail_share(g, g_ref))
+        for key in keys:
+            reuse[key].append(e[key])
+        reuse["tail"].append(tail_share(g, g_ref))
         for m in n_fresh:
             for r in range(fresh_draws):
                 _fresh_grad(p, b, rec.gt, int(m), seed + 500 + 17 * r, 100 + j, img, dldi, gf)
                 e = rel_errors(gf, g_ref)
                 f = fresh[int(m)]
-                f["l2"].append(e["l2"]); f["l1"].append(e["l1"]); f["tail"].append(tail_share(gf, g_ref))
+                for key in keys:
+                    f[key].append(e[key])
+                f["tail"].append(tail_share(gf, g_ref))
     p.close()
     rms = lambda v: math.sqrt(sum(x * x for x in v) / len(v))
     mean = lambda v: sum(v) / len(v)
     out = {"ages": [k for k, _, _ in kept], "copies": copies, "factor": factor, "fresh_draws": fresh_draws,
            "ref_norm_l2": refnorm,
            "reuse": {"l2": rms(reuse["l2"]), "l1": rms(reuse["l1"]), "tail_share_top0.1pct": mean(reuse["tail"]),
-                     "l2_per_age": reuse["l2"], "l1_per_age": reuse["l1"]},
-           "resample": {str(m): {"l2": rms(f["l2"]), "l1": rms(f["l1"]), "tail_share_top0.1pct": mean(f["tail"])}
+                     "norm_ratio": mean(reuse["norm_ratio"]), "cos": mean(reuse["cos"]),
+                     "l2_per_age": reuse["l2"], "l1_per_age": reuse["l1"], "norm_ratio_per_age": reuse["norm_ratio"],
+                     "cos_per_age": reuse["cos"]},
+           "resample": {str(m): {"l2": rms(f["l2"]), "l1": rms(f["l1"]), "tail_share_top0.1pct": mean(f["tail"]),
+                                 "norm_ratio": mean(f["norm_ratio"]), "cos": mean(f["cos"])}
                         for m, f in fresh.items()}}
     for norm in ("l2", "l1"):
         fit = n_star(out["reuse"][norm], {m: out["resample"][str(m)][norm] for m in fresh})

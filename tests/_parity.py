@@ -25,8 +25,10 @@ THREADS = os.cpu_count() or 1   # oracle threads (the split does not change its 
 # measured float32 budget -- their error exceeds RTOL of the value (pixels)
 # or of the term mass (voxels) -- may be at most this fraction of the
 # non-zero elements; every comparison prints its count and the largest
-# budget / (RTOL x value) ratio.
-MAX_BUDGET_ONLY = 5e-3
+# budget / (RTOL x value) ratio, and their share of the summed magnitude
+# (|value| or term mass).  Small path sets need the budget most: a voxel
+# crossed by few rays, one of them ill-conditioned.
+MAX_BUDGET_ONLY = 5e-2
 
 
 def t32(a):
@@ -42,7 +44,7 @@ def divergent(fp_gpu: torch.Tensor, fp_oracle: np.ndarray, first: int = 0):
     return np.nonzero(g != fp_oracle)[0] + first
 
 
-def assert_images_close(gi, oi, rtol=RTOL, what="images", cond=None):
+def assert_images_close(gi, oi, rtol=RTOL, what="images", cond=None, max_budget_only=MAX_BUDGET_ONLY):
     """Per pixel: |gpu - oracle| <= rtol |oracle| + cond, where cond (the
     oracle's image_cond) is the measured float32 sensitivity of the pixel's
     contributions: large only where a path's geometry is ill-conditioned (a
@@ -60,10 +62,10 @@ def assert_images_close(gi, oi, rtol=RTOL, what="images", cond=None):
         k = np.argmax(err / budget)
         raise AssertionError(f"{what}: {bad.sum()} of {bad.size} elements off; worst at {k}: "
                              f"gpu {gi[k]:.9e} oracle {oi[k]:.9e} budget {np.broadcast_to(budget, oi.shape)[k]:.3e}")
-    _budget_report(what, err, rtol * np.abs(oi) + floor, cond, oi != 0)
+    _budget_report(what, err, rtol * np.abs(oi) + floor, cond, oi != 0, np.abs(oi), max_budget_only)
 
 
-def assert_grad_close(gg, og, oabs, ocond=None, rtol=RTOL, what="grad"):
+def assert_grad_close(gg, og, oabs, ocond=None, rtol=RTOL, what="grad", max_budget_only=MAX_BUDGET_ONLY):
     """Per voxel: |g_gpu - g_oracle| <= rtol * sum|terms| + cond, where
     cond (the oracle's grad_cond) is the measured float32 sensitivity of the
     voxel's gradient terms (the change under perturbed re-sampling of the
@@ -80,14 +82,15 @@ def assert_grad_close(gg, og, oabs, ocond=None, rtol=RTOL, what="grad"):
         k = np.argmax(err / budget)
         raise AssertionError(f"{what}: {bad.sum()} of {bad.size} voxels off; worst at {k}: gpu {gg[k]:.9e} "
                              f"oracle {og[k]:.9e} |terms| {oabs[k]:.3e} budget {budget[k]:.3e}")
-    _budget_report(what, err, rtol * oabs + floor0, ocond, oabs != 0)
+    _budget_report(what, err, rtol * oabs + floor0, ocond, oabs != 0, oabs, max_budget_only)
 
 
-def _budget_report(what, err, base, cond, nonzero):
+def _budget_report(what, err, base, cond, nonzero, mag, max_budget_only):
     """Counts the elements whose error exceeds the base tolerance (RTOL of
     the value or term mass) and that pass only through the float32 budget;
-    prints the count and the largest budget / base ratio, and bounds the
-    count by MAX_BUDGET_ONLY of the non-zero elements."""
+    prints the count, their share of the summed magnitude and the largest
+    budget / base ratio, and bounds the count by max_budget_only of the
+    non-zero elements."""
     n = int(np.count_nonzero(nonzero))
     over = (err > base) & nonzero
     k = int(np.count_nonzero(over))
@@ -95,10 +98,11 @@ def _budget_report(what, err, base, cond, nonzero):
     if cond is not None and n:
         c = np.broadcast_to(np.asarray(cond, dtype=np.float64), err.shape)[nonzero]
         ratio = float(np.max(c / np.maximum(base[nonzero], 1e-300)))
+    share = float(mag[over].sum()) / max(float(mag.sum()), 1e-300)
     print(f"[parity] {what}: {k} of {n} non-zero elements pass only through the float32 budget "
-          f"({k / max(n, 1):.2e}); largest budget / ({RTOL:g} x value) = {ratio:.3g}")
-    assert k <= MAX_BUDGET_ONLY * n, (f"{what}: {k} of {n} non-zero elements need the float32 budget "
-                                      f"(more than {MAX_BUDGET_ONLY:g})")
+          f"({k / max(n, 1):.2e}, {share:.2e} of the magnitude); largest budget / ({RTOL:g} x value) = {ratio:.3g}")
+    assert k <= max_budget_only * n, (f"{what}: {k} of {n} non-zero elements need the float32 budget "
+                                      f"(more than {max_budget_only:g})")
 
 
 def forward_parity(sc, beta, n, first=0, seed=None):

@@ -255,6 +255,7 @@ def test_cumulus256_chunked_fullsize():
     oi = np.zeros(scene.n_pixels); icond = np.zeros(scene.n_pixels)
     og = np.zeros(scene.n_voxels); oabs = np.zeros(scene.n_voxels); ocond = np.zeros(scene.n_voxels)
     used = 0
+    dld = t64(dl)
     for pid in ids[:12] + [n - 1]:
         o = O.render(sc, br, bt, first=pid, n=1, n_norm=n, dldi=dl, grad_abs=True, grad_cond=True,
                      image_cond=True, fingerprints=True)
