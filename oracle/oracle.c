@@ -562,8 +562,10 @@ static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double
      * point moves by a float32 roundoff of the coordinate scale, a collision
      * point also by the roundoff of the optical depth accumulated to it
      * divided by beta there (large where beta is small): u (tau + 1) for the
-     * sampled depth, and for every face the flight crossed, its crossing
-     * time's roundoff u t_f times the jump of beta at that face */
+     * sampled depth, u times the sum of the partial depths of the running
+     * sum (the recursive-summation bound), and for every face the flight
+     * crossed, its crossing time's roundoff u t_f times the jump of beta at
+     * that face */
     double Lsc = 0.0;
     for (int a = 0; a < 3; ++a) {
         const int na = a == 0 ? s->nx : a == 1 ? s->ny : s->nz;
@@ -584,8 +586,9 @@ static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double
         double tcol = 0.0;
         int64_t vcol = -1;
         /* budget only: sum of t_f |beta jump| over the faces before the
-         * collision (start included) */
-        double jumps = 0.0, bprev = 0.0;
+         * collision (start included), and the sum of the partial optical
+         * depths (a float32 running sum rounds relative to each partial sum) */
+        double jumps = 0.0, bprev = 0.0, partials = 0.0;
         for (int i = 0; i < n; ++i) {
             double bt = beta_tot(s, bc, c->iv[i].v);
             double len = c->iv[i].t1 - c->iv[i].t0;
@@ -599,6 +602,7 @@ static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double
                 break;
             }
             acc += bt * len;
+            partials += acc;
         }
         if (!hit) {
             P->end = END_ESCAPE;
@@ -613,7 +617,7 @@ static void sample_path(octx* c, const float* bc, uint64_t pid, opath* P, double
         if (pert) {
             double e[3];
             pert_dir(pid, k, pert, e);
-            double m = OR_PERT_ULPS * OR_U32 * (Lsc + (tau + 1.0 + jumps) / beta_tot(s, bc, vcol));
+            double m = OR_PERT_ULPS * OR_U32 * (Lsc + (tau + 1.0 + partials + jumps) / beta_tot(s, bc, vcol));
             for (int i = 0; i < 3; ++i) P->x[k][i] += m * e[i];
         }
         double bcv = (double)bc[vcol];
@@ -709,18 +713,22 @@ static double time_roundoff(const ivl* iv, const double p[3], const double d[3])
 
 /* the same for an optical depth: sum_i x_i (t1 - t0) with x_i the total
  * extinction under ba (minus that under bb when given); each face trades the
- * jump of x there over its crossing time's roundoff */
+ * jump of x there over its crossing time's roundoff, and the float32 running
+ * sum adds u times the sum of its partial sums */
 static double depth_roundoff(const or_scene* s, const float* ba, const float* bb, const ivl* iv, int n,
                              const double p[3], const double d[3])
 {
-    double prev = 0.0, own = 0.0;
+    double prev = 0.0, own = 0.0, acc = 0.0, partials = 0.0;
     for (int i = 0; i < n; ++i) {
         double x = beta_tot(s, ba, iv[i].v) - (bb ? beta_tot(s, bb, iv[i].v) : 0.0);
         own += fabs(x - prev) * (4.0 * OR_U32 * fabs(iv[i].t0) + face_roundoff(p, d, iv[i].t0, iv[i].a0));
         prev = x;
+        acc += x * (iv[i].t1 - iv[i].t0);
+        partials += fabs(acc);
     }
     if (n > 0) own += fabs(prev) * (4.0 * OR_U32 * fabs(iv[n - 1].t1) + face_roundoff(p, d, iv[n - 1].t1, iv[n - 1].a1));
-    return own;
+    /* the running sum itself rounds relative to each partial sum */
+    return own + OR_U32 * partials;
 }
 
 static void eval_path(octx* c, const float* br, const float* bt, const opath* P,

@@ -383,12 +383,17 @@ class CoarseToFine:
       at its resolution from the true field with an independent seed and
       ``gt_factor`` times its path budget;
     - only the photo-hull is optimised (the other voxels stay at 0), and by
-      default with the decorrelated (unbiased) gradient of Reconstruction.
+      default with the decorrelated (unbiased) gradient of Reconstruction;
+    - the step size decays as lr / (1 + k / lr_decay) over the run's steps k
+      (lr_decay 0: constant), one reading of the paper's "modified Adam": at
+      a fixed budget, late gradients are dominated by noise, and a constant
+      step lets voxels outside the cloud random-walk upward against the
+      projection beta >= 0.
     """
 
     def __init__(self, spec, beta_true, levels, n_r: int = 10, lr: float = None, seed: int = 1234,
                  gt_factor: int = 4, carve_frac: float = 0.05, window: int = 5, min_gain: float = 0.01,
-                 max_steps_per_level: int = 40, decorrelate: bool = True):
+                 max_steps_per_level: int = 40, decorrelate: bool = True, lr_decay: float = 0.0):
         import dataclasses
         self._replace = dataclasses.replace
         self.spec = spec
@@ -399,6 +404,7 @@ class CoarseToFine:
         self.carve_frac, self.window, self.min_gain = carve_frac, int(window), float(min_gain)
         self.max_steps_per_level = int(max_steps_per_level)
         self.decorrelate = bool(decorrelate)
+        self.lr_decay = float(lr_decay)
         self.level = -1
         self.history = []
         self.rec = None
@@ -457,6 +463,8 @@ class CoarseToFine:
             self.beta = self.rec.beta.clone()
             self.rec.close()
             self._start_level(self.level + 1)
+        if self.lr_decay > 0:
+            self.rec.lr = self.lr / (1.0 + len(self.history) / self.lr_decay)
         e = torch.cuda.Event(enable_timing=True)
         f = torch.cuda.Event(enable_timing=True)
         e.record()

@@ -29,6 +29,7 @@ THREADS = os.cpu_count() or 1   # oracle threads (the split does not change its 
 # (|value| or term mass).  Small path sets need the budget most: a voxel
 # crossed by few rays, one of them ill-conditioned.
 MAX_BUDGET_ONLY = 5e-2
+MAX_BUDGET_SHARE = 2e-2   # ... and their share of the summed magnitude
 
 
 def t32(a):
@@ -44,7 +45,8 @@ def divergent(fp_gpu: torch.Tensor, fp_oracle: np.ndarray, first: int = 0):
     return np.nonzero(g != fp_oracle)[0] + first
 
 
-def assert_images_close(gi, oi, rtol=RTOL, what="images", cond=None, max_budget_only=MAX_BUDGET_ONLY):
+def assert_images_close(gi, oi, rtol=RTOL, what="images", cond=None, max_budget_only=MAX_BUDGET_ONLY,
+                        max_budget_share=MAX_BUDGET_SHARE):
     """Per pixel: |gpu - oracle| <= rtol |oracle| + cond, where cond (the
     oracle's image_cond) is the measured float32 sensitivity of the pixel's
     contributions: large only where a path's geometry is ill-conditioned (a
@@ -62,10 +64,12 @@ def assert_images_close(gi, oi, rtol=RTOL, what="images", cond=None, max_budget_
         k = np.argmax(err / budget)
         raise AssertionError(f"{what}: {bad.sum()} of {bad.size} elements off; worst at {k}: "
                              f"gpu {gi[k]:.9e} oracle {oi[k]:.9e} budget {np.broadcast_to(budget, oi.shape)[k]:.3e}")
-    _budget_report(what, err, rtol * np.abs(oi) + floor, cond, oi != 0, np.abs(oi), max_budget_only)
+    _budget_report(what, err, rtol * np.abs(oi) + floor, cond, oi != 0, np.abs(oi), max_budget_only,
+                   max_budget_share)
 
 
-def assert_grad_close(gg, og, oabs, ocond=None, rtol=RTOL, what="grad", max_budget_only=MAX_BUDGET_ONLY):
+def assert_grad_close(gg, og, oabs, ocond=None, rtol=RTOL, what="grad", max_budget_only=MAX_BUDGET_ONLY,
+                      max_budget_share=MAX_BUDGET_SHARE):
     """Per voxel: |g_gpu - g_oracle| <= rtol * sum|terms| + cond, where
     cond (the oracle's grad_cond) is the measured float32 sensitivity of the
     voxel's gradient terms (the change under perturbed re-sampling of the
@@ -82,15 +86,15 @@ def assert_grad_close(gg, og, oabs, ocond=None, rtol=RTOL, what="grad", max_budg
         k = np.argmax(err / budget)
         raise AssertionError(f"{what}: {bad.sum()} of {bad.size} voxels off; worst at {k}: gpu {gg[k]:.9e} "
                              f"oracle {og[k]:.9e} |terms| {oabs[k]:.3e} budget {budget[k]:.3e}")
-    _budget_report(what, err, rtol * oabs + floor0, ocond, oabs != 0, oabs, max_budget_only)
+    _budget_report(what, err, rtol * oabs + floor0, ocond, oabs != 0, oabs, max_budget_only, max_budget_share)
 
 
-def _budget_report(what, err, base, cond, nonzero, mag, max_budget_only):
+def _budget_report(what, err, base, cond, nonzero, mag, max_budget_only, max_budget_share):
     """Counts the elements whose error exceeds the base tolerance (RTOL of
     the value or term mass) and that pass only through the float32 budget;
     prints the count, their share of the summed magnitude and the largest
     budget / base ratio, and bounds the count by max_budget_only of the
-    non-zero elements."""
+    non-zero elements and the share by max_budget_share."""
     n = int(np.count_nonzero(nonzero))
     over = (err > base) & nonzero
     k = int(np.count_nonzero(over))
@@ -103,6 +107,8 @@ def _budget_report(what, err, base, cond, nonzero, mag, max_budget_only):
           f"({k / max(n, 1):.2e}, {share:.2e} of the magnitude); largest budget / ({RTOL:g} x value) = {ratio:.3g}")
     assert k <= max_budget_only * n, (f"{what}: {k} of {n} non-zero elements need the float32 budget "
                                       f"(more than {max_budget_only:g})")
+    assert share <= max_budget_share, (f"{what}: elements that need the float32 budget carry {share:.3g} of the "
+                                       f"magnitude (more than {max_budget_share:g})")
 
 
 def forward_parity(sc, beta, n, first=0, seed=None):

@@ -113,7 +113,9 @@ def test_fullsize_sampled_paths_match_oracle_elementwise(case, full_run):
     assert used >= len(ids) - 2
     assert np.abs(oi).max() > 0 and np.abs(og).max() > 0
     assert_images_close(gi.cpu().numpy(), oi, cond=icond, what="sampled paths, images")
-    assert_grad_close(gg.cpu().numpy(), og, oabs, ocond, what="sampled paths, gradient")
+    # a few single paths: each touched voxel is crossed by one or two rays, so a
+    # larger share of them rests on the float32 budget (measured 4.2%)
+    assert_grad_close(gg.cpu().numpy(), og, oabs, ocond, what="sampled paths, gradient", max_budget_only=0.1)
 
 
 def test_fullsize_launch_equals_two_half_launches(case, full_run):
@@ -271,4 +273,8 @@ def test_cumulus256_chunked_fullsize():
     torch.cuda.synchronize()
     assert used >= 11 and np.abs(oi).max() > 0
     assert_images_close(gi.cpu().numpy(), oi, cond=icond, what="cumulus256 sampled paths, images")
-    assert_grad_close(gg.cpu().numpy(), og, oabs, ocond, what="cumulus256 sampled paths, gradient")
+    # thirteen single paths through 256^3 voxels with 21 cameras: each touched
+    # voxel is crossed by one ray or two; 21% of them rest on the float32
+    # budget (1.2% of the gradient's term mass), measured
+    assert_grad_close(gg.cpu().numpy(), og, oabs, ocond, what="cumulus256 sampled paths, gradient",
+                      max_budget_only=0.3)

@@ -127,6 +127,22 @@ def test_coarse_to_fine_reconstruction_moves_toward_the_truth():
     assert hist[-1]["eps"] < eps0 and abs(hist[-1]["delta"]) < abs(delta0)
 
 
+def test_reconstruction_reaches_a_stated_error():
+    """The same 32^3 field seen by its 9 cameras at 64x64 pixels, 2^24 paths
+    per step (512 per voxel), hull carved at 20% of the mean lit pixel, a
+    decaying step (max/100 / (1 + k/30)), 150 Adam steps of Alg. 2: the
+    relative L1 error falls from about 1.05 to below 0.8 and the mass bias
+    stays within 20% (measured: eps 0.72, delta -0.13)."""
+    sc = synth.config(1, n_paths=1 << 24)
+    beta_true = torch.from_numpy(sc.beta_cloud.reshape(-1).astype(np.float32)).cuda()
+    c2f = CoarseToFine(sc, beta_true, levels=[(64, 1 << 24)], n_r=10, lr=float(beta_true.max()) / 100,
+                       carve_frac=0.2, min_gain=-1e9, max_steps_per_level=150, lr_decay=30.0)
+    hist = c2f.run(150)
+    assert len(hist) == 150
+    assert hist[0]["eps"] > 0.95
+    assert hist[-1]["eps"] < 0.8 and abs(hist[-1]["delta"]) < 0.2
+
+
 def test_reconstruction_checkpoint_resume_repeats_steps():
     """A snapshot taken at a resample boundary and restored repeats the same
     Adam steps (same paths: seeds and epoch come back with it)."""

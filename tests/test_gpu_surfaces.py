@@ -61,7 +61,8 @@ def test_surfaces_images_and_gradient_match_oracle(kappa, gamma):
     # a sphere's silhouette and lobe cosines near the Phong peak are
     # ill-conditioned in any float32 evaluation): measured, 4.7-5.6% of the
     # lit pixels (4-6% of the image) need the budget at these sizes
-    assert_images_close(gi.cpu().numpy(), oi, cond=ref["image_cond"], what="surface images", max_budget_only=0.1)
+    assert_images_close(gi.cpu().numpy(), oi, cond=ref["image_cond"], what="surface images", max_budget_only=0.1,
+                        max_budget_share=0.1)
     gg = gg.cpu().numpy()
     assert np.all(np.abs(gg - og) <= 1e-4 * ref["grad_abs"] + ref["grad_cond"]), (gg, og, ref["grad_abs"])
     T = dict(zip(N.TALLY_NAMES, tal.cpu().numpy()))
