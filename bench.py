@@ -562,11 +562,12 @@ def run_ablation(args, ws, rank, local):
 
 def run_recon(args, ws, rank, local):
     """The reconstruction of Sec. 6 on the 32^3 blob field (9 cameras at
-    64x64 pixels): hull carved at 20% of the mean lit pixel, then Alg. 2
-    with 2^26 paths per step (2048 per voxel; decorrelated gradient, hull
-    only, N_r = 10), step max/100 decaying as 1/(1 + k/30), --recon-steps
-    Adam steps; reports eps and delta at the start and the end, the
-    trajectory and the time per step.  (At 8-16 paths per voxel the
+    64x64 pixels): hull carved at --recon-carve (0.2) of the mean lit pixel,
+    then Alg. 2 with 2^26 paths per step (2048 per voxel; --paths; the
+    decorrelated gradient, hull only, N_r = 10), step max/100 (--recon-lr-div)
+    decaying as 1/(1 + k/30) (--recon-decay), --recon-steps Adam steps;
+    reports eps and delta at the start and the end, the trajectory and the
+    time per step.  (At 8-16 paths per voxel the
     gradient is noise: its cosine to a 64x-budget reference is 0.67 at 2^22
     paths, 0.89 at 2^24 and 0.97 at 2^26 on this field's start.)"""
     import numpy as np
@@ -581,14 +582,39 @@ def run_recon(args, ws, rank, local):
     sc = synth.config(1, n_paths=n)
     bt = torch.from_numpy(sc.beta_cloud.reshape(-1).astype(np.float32)).cuda()
     steps = int(args.recon_steps)
-    c2f = CoarseToFine(sc, bt, levels=[(64, n)], n_r=N_R, lr=float(bt.max()) / 100, carve_frac=0.2,
-                       min_gain=-1e9, max_steps_per_level=steps, lr_decay=30.0, seed=sc.seed + rank)
+    c2f = CoarseToFine(sc, bt, levels=[(64, n)], n_r=N_R, lr=float(bt.max()) / args.recon_lr_div,
+                       carve_frac=args.recon_carve, min_gain=-1e9, max_steps_per_level=steps,
+                       lr_decay=args.recon_decay, seed=sc.seed + rank)
     try:
         pr = torch.cuda.get_device_properties(local)
         gpu_id = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
     except Exception:
         gpu_id = str(local)
     clocks = Clocks(gpu_id)
+    snr = None
+    if args.recon_snr:
+        # the gradient's signal at the start state: cosine of fresh gradients
+        # to the mean of 16 gradients of 4x the budget (calibrate.reference_gradient)
+        from paper_2110_00085_gb300 import calibrate as CAL
+        from paper_2110_00085_gb300 import native as N
+        scene0, gt0 = c2f._level(0)
+        lit = gt0[gt0 > 0]
+        hull0 = scene0.space_carve(gt0, args.recon_carve * float(lit.mean()))
+        b0 = hull0.to(torch.float32) * CoarseToFine.cloud_mean(bt)
+        snr = {}
+        for m in (n // 16, n // 4, n):
+            g_ref = CAL.reference_gradient(scene0, gt0, b0, m, copies=16, factor=4, seed=555)
+            p = N.Paths(scene0)
+            img = scene0.new_images()
+            dl = torch.zeros_like(img)
+            g = torch.zeros(scene0.n_voxels, dtype=torch.float64, device=img.device)
+            es = []
+            for r in range(3):
+                CAL._fresh_grad(p, b0, gt0, m, 900 + r, 0, img, dl, g)
+                es.append(CAL.rel_errors(g, g_ref))
+            p.close()
+            snr[str(m)] = {"cos": [round(e["cos"], 4) for e in es], "l2": [round(e["l2"], 4) for e in es]}
+        scene0.close()
     barrier(ws)
     clocks.start()
     w0 = time.perf_counter()
@@ -607,15 +633,16 @@ def run_recon(args, ws, rank, local):
     out = {"metric": METRIC, "value": ws * paths / (step_ms * 1e-3), "unit": UNIT, "n_gpus": ws,
            "steps": len(hist), "warmup": 0, "ms_per_step": step_ms / len(hist), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"recon: 32^3 blobs (peak 20/km), 9 cameras at 64x64, hull carved at 20% of the "
-                                  f"mean lit pixel, {n} paths per step, N_r=10, decorrelated gradient, step "
-                                  f"max/100 / (1 + k/30), {steps} steps",
+           "config": {"workload": f"recon: 32^3 blobs (peak 20/km), 9 cameras at 64x64, hull carved at "
+                                  f"{args.recon_carve:g} of the mean lit pixel, {n} paths per step, N_r=10, "
+                                  f"decorrelated gradient, step max/{args.recon_lr_div:g} / (1 + k/"
+                                  f"{args.recon_decay:g}), {steps} steps",
                       "hull_fraction": float(c2f.hull.float().mean())},
            "recon": {"eps_start": eps0, "delta_start": delta0, "eps_end": hist[-1]["eps"],
                      "delta_end": hist[-1]["delta"], "eps_min": min(h["eps"] for h in hist),
                      "eps_every_25": [round(h["eps"], 4) for h in hist[::25]],
                      "delta_every_25": [round(h["delta"], 4) for h in hist[::25]],
-                     "levels": levels, "wall_s": wall,
+                     "levels": levels, "wall_s": wall, "start_gradient_signal": snr,
                      "note": "ms_per_step: CUDA events around each Adam step (resamples included); wall_s also "
                              "covers the ground-truth renders of each level and the carving"},
            "clocks": ck}
@@ -1020,6 +1047,13 @@ def main():
                     choices=list(CONFIGS) + ["batch", "recon", "surfaces", "peaks", "ablation"])
     ap.add_argument("--surf-steps", type=int, default=800, help="surfaces workload: Adam steps per arm")
     ap.add_argument("--recon-steps", type=int, default=600, help="recon workload: Adam steps")
+    ap.add_argument("--recon-carve", type=float, default=0.2,
+                    help="recon workload: clear-pixel threshold of the carving, x mean lit pixel")
+    ap.add_argument("--recon-lr-div", type=float, default=100.0, help="recon workload: step = max extinction / this")
+    ap.add_argument("--recon-decay", type=float, default=30.0,
+                    help="recon workload: step decay 1/(1 + k/this); 0 = constant step")
+    ap.add_argument("--recon-snr", action="store_true",
+                    help="recon workload: first measure the start state's gradient cosine to a reference")
     ap.add_argument("--path-scale", type=int, default=0, help="batch workload: lower every 2^k path budget by k")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
