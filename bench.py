@@ -885,7 +885,8 @@ def run_native(args, ws, rank, local):
     lr = float(gt_np.max()) / 50.0
 
     def make(n_r):
-        return Reconstruction(scene, gt_img, beta0, n, n_r=n_r, lr=lr, seed=sc.seed + rank, cache=True)
+        return Reconstruction(scene, gt_img, beta0, n, n_r=n_r, lr=lr, seed=sc.seed + rank, cache=True,
+                              lean=args.lean)
 
     # ---- algorithmic work per pass: voxel crossings of the stored paths ----
     tal = torch.zeros(N.TALLY_COUNT, dtype=torch.float64, device=dev)
@@ -924,6 +925,9 @@ def run_native(args, ws, rank, local):
     gpu_launches = rec.launches - launches0
     ms = max_over_ranks(ws, ms)
     info = rec.paths.info()
+    free_b, total_b = torch.cuda.mem_get_info(dev)
+    memory = {"stored_paths_gb": info["bytes_device"] / 1e9, "device_used_gb": (total_b - free_b) / 1e9,
+              "device_total_gb": total_b / 1e9}
     kern = {k: [a.elapsed_time(b) for a, b in v] for k, v in timers.items()}
     scene.check()
     rec.paths.close()
@@ -1004,9 +1008,10 @@ def run_native(args, ws, rank, local):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": CONFIGS[args.workload][1], "n_paths": n, "n_r": N_R, "replicas": ws,
+                   "lean_cache": bool(args.lean and n > (1 << 26)),
                    "accumulation": "f64 pixel and gradient sums",
                    "l2": "inputs larger than L2 (stored paths and contribution cache, GBs per step)",
-                   "stored_paths": int(info["n_stored"]), "records": int(info["n_records"]),
+                   "stored_paths": int(info["n_stored"]), "records": int(info["n_records"]), "memory": memory,
                    "mean_collisions": T["collisions"] / max(T["entered"], 1.0)},
         "resample": {"ms_per_step": ms_res, "value": ws * n / (ms_res * 1e-3), "unit": UNIT,
                      "note": "Alg. 1 at the same path budget"},
@@ -1047,6 +1052,8 @@ def main():
                     choices=list(CONFIGS) + ["batch", "recon", "surfaces", "peaks", "ablation"])
     ap.add_argument("--surf-steps", type=int, default=800, help="surfaces workload: Adam steps per arm")
     ap.add_argument("--recon-steps", type=int, default=600, help="recon workload: Adam steps")
+    ap.add_argument("--lean", action="store_true",
+                    help="path sets above 2^26: keep one chunk's contribution cache at a time")
     ap.add_argument("--recon-carve", type=float, default=0.2,
                     help="recon workload: clear-pixel threshold of the carving, x mean lit pixel")
     ap.add_argument("--recon-lr-div", type=float, default=100.0, help="recon workload: step = max extinction / this")

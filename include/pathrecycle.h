@@ -63,6 +63,8 @@ extern "C" {
                                  so that each re-evaluation merges same-pixel
                                  terms before its FP64 adds (pays off when the
                                  paths are re-evaluated more than once)       */
+#define PT_ASYNC 8u           /* paths_store: do not synchronise the stream;
+                                 see paths_store                             */
 
 /* tallies: float64[PT_TALLY_COUNT], same meaning as the CPU oracle's */
 enum {
@@ -161,6 +163,16 @@ int render_forward(const pt_scene* scene, const float* beta_cloud,
  * nothing and leaves the handle without paths.
  * n_paths < 2^32 per handle; larger path sets are stored as several handles
  * over ranges of path ids (first_path) sharing n_norm.
+ * PT_ASYNC (on a handle that an earlier store of this scene has sized):
+ * nothing synchronises and nothing is allocated but the transient records
+ * (stream-ordered).  The extinction check and the fit of the new path set
+ * in the handle's buffers are made on the device instead: an invalid grid,
+ * or more records or events than the buffers hold, leaves the handle
+ * holding no paths (later passes add nothing) and sets bit 8 of the
+ * scene's error word, which pt_check reports as PT_E_DEVICE_ASSERT.
+ * Callers that use it check pt_check (a store of a similar path set after a
+ * synchronous one fits: the buffers keep 1/8 headroom).  On a handle not
+ * yet sized, PT_ASYNC is ignored.
  */
 int paths_store(const pt_scene* scene, const float* beta_cloud,
                 uint64_t first_path, uint64_t n_paths, double n_norm,
@@ -210,6 +222,17 @@ int render_grad(pt_paths* paths, const float* beta_t, const double* dL_dI,
 uint64_t paths_cache_token(const pt_paths* paths);
 
 int paths_free(pt_paths* paths);
+
+/*
+ * paths_drop_cache -- frees the handle's contribution cache (4 bytes per
+ * event and camera, the largest buffer of a stored path set) and
+ * invalidates it; the next paths_reweight(PT_CACHE) allocates it again.
+ * For path sets stored as several handles whose caches do not fit side by
+ * side: reweight every handle without the cache for the images, then per
+ * handle reweight with the cache, take its gradient and drop the cache.
+ * Synchronises the device (cudaFree); never fails on a null handle.
+ */
+int paths_drop_cache(pt_paths* paths);
 /* Synchronises the stream; fills counts of the latest store. */
 int paths_info(const pt_paths* paths, pt_paths_info* out, void* stream);
 
@@ -416,11 +439,13 @@ int render_forward_static(const pt_scene_desc* desc, const float* beta_cloud,
 /* Synchronises the stream and reports (then clears) kernel-side invariant
  * violations recorded in the scene: PT_E_DEVICE_ASSERT, the text naming the
  * bits (1 voxel index out of range, 2 traversal longer than the grid allows,
- * 4 stored record with an invalid voxel). */
+ * 4 stored record with an invalid voxel, 8 a paths_store(PT_ASYNC) whose path
+ * set did not fit the handle's buffers or whose extinction grid was
+ * invalid). */
 int pt_check(const pt_scene* scene, void* stream);
 
-/* Test hook for the reporting path: ORs `bits` (1, 2, 4 as above) into the
- * scene's device error word on the stream, as a kernel that detected the
+/* Test hook for the reporting path: ORs `bits` (1..15, the bits above) into
+ * the scene's device error word on the stream, as a kernel that detected the
  * violation would, without running any kernel. */
 int pt_inject_error(pt_scene* scene, int bits, void* stream);
 

@@ -211,6 +211,7 @@ struct pt_paths {
     float4* sb = nullptr;      // sorted records (stream B)
     Buckets* bk = nullptr;
     uint32_t* bad = nullptr;   // invalid extinction voxels found by the store's check
+    uint32_t* abort_flag = nullptr;   // PT_ASYNC: the latest store did not fit (device)
     Events ev{};               // ev.cap = events the buffers hold
     float* cache = nullptr;
     uint64_t cache_cap = 0;    // floats
@@ -264,7 +265,9 @@ cudaMemPool_t store_pool() {
 void free_paths_buffers(pt_paths* p) {
     cudaFree(p->beta_ref); cudaFree(p->dbeta); cudaFree(p->sa); cudaFree(p->sb); cudaFree(p->bk); cudaFree(p->cache);
     cudaFree(p->bad);
+    cudaFree(p->abort_flag);
     p->bad = nullptr;
+    p->abort_flag = nullptr;
     cudaFree(p->ev.a); cudaFree(p->ev.b); cudaFree(p->ev.of_rec); cudaFree(p->ev.val); cudaFree(p->ev.hist);
     cudaFree(p->ev.cursor); cudaFree(p->ev.partial);
     p->beta_ref = p->dbeta = nullptr; p->sa = nullptr; p->sb = nullptr;
@@ -517,6 +520,7 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
             (rc = dev_alloc(&p->dbeta, (uint64_t)p->V, &by, "dbeta")) ||
             (rc = dev_alloc(&p->bk, 1, &by, "buckets")) ||
             (rc = dev_alloc(&p->bad, 1, &by, "extinction check")) ||
+            (rc = dev_alloc(&p->abort_flag, 1, &by, "store fit flag")) ||
             (rc = dev_alloc(&E.hist, E.n_bins, &by, "event bins")) ||
             (rc = dev_alloc(&E.cursor, E.n_bins, &by, "event bin cursors")) ||
             (rc = dev_alloc(&E.partial, 3 * 4096, &by, "scan partials"))) {
@@ -531,10 +535,16 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
     p->inv_norm = (float)(1.0 / n_norm);
     set_cache(p, false, nullptr);
     *pp = p;
+    // PT_ASYNC on a sized handle: the checks run on the device (see the header)
+    const bool async = (flags & PT_ASYNC) && p->sa && p->ev.a && p->rec_cap > 0 && p->ev.cap > 0;
 
     // no path kernel runs on an extinction grid with NaN, infinite or negative
     // voxels: count them first (one synchronisation; the store has another)
-    {
+    if (async) {
+        PT_CUDA(cudaMemsetAsync(p->bad, 0, sizeof(uint32_t), st));
+        k_check_beta<<<grid_for(p->V, 256), 256, 0, st>>>(beta, p->V, p->bad);
+        if ((rc = launch_status("paths_store check"))) return rc;
+    } else {
         uint32_t bad = 0;
         PT_CUDA(cudaMemsetAsync(p->bad, 0, sizeof(uint32_t), st));
         k_check_beta<<<grid_for(p->V, 256), 256, 0, st>>>(beta, p->V, p->bad);
@@ -583,6 +593,14 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
     if ((rc = launch_status("paths_store"))) { release(); return rc; }
     launch_sort_count(sbuf, n, slots, blk, p->bk, st);
     if ((rc = launch_status("paths_store sort"))) { release(); return rc; }
+    if (async) {
+        launch_store_guard(p->bk, p->rec_cap, p->ev.cap, p->bad, p->abort_flag, sc->d_err, st);
+        launch_sort_scatter(sbuf, n, blk, p->bk, p->sa, p->sb, st, p->abort_flag);
+        release();
+        if ((rc = launch_status("paths_store sort"))) return rc;
+        launch_events(sc->ds, sorted_view(p), p->ev, st);
+        return launch_status("paths_store events");
+    }
     Buckets hb;
     if (cudaMemcpyAsync(&hb, p->bk, sizeof(Buckets), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
@@ -673,6 +691,19 @@ int render_grad(pt_paths* p, const float* beta_t, const double* dldi, double* gr
 }
 
 uint64_t paths_cache_token(const pt_paths* p) { return p && p->cache_valid ? p->cache_token : 0; }
+
+int paths_drop_cache(pt_paths* p) {
+    if (!p) return PT_OK;
+    if (p->cache) {
+        const cudaError_t e = cudaFree(p->cache);
+        if (e != cudaSuccess) return fail(PT_E_CUDA, "paths_drop_cache: %s", cudaGetErrorString(e));
+    }
+    p->cache = nullptr;
+    p->bytes -= p->cache_cap * sizeof(float);
+    p->cache_cap = 0;
+    set_cache(p, false, nullptr);
+    return PT_OK;
+}
 
 int paths_free(pt_paths* p) {
     if (!p) return PT_OK;
@@ -919,7 +950,9 @@ int pt_check(const pt_scene* sc, void* stream) {
     if (h) {
         PT_CUDA(cudaMemsetAsync(sc->d_err, 0, sizeof(int), S_(stream)));
         PT_CUDA(cudaStreamSynchronize(S_(stream)));
-        return fail(PT_E_DEVICE_ASSERT, "kernel invariant violated (bits 0x%x: 1 index, 2 traversal length, 4 record)",
+        return fail(PT_E_DEVICE_ASSERT,
+                    "kernel invariant violated (bits 0x%x: 1 index, 2 traversal length, 4 record, 8 a PT_ASYNC store "
+                    "did not fit its buffers or had an invalid extinction grid)",
                     h);
     }
     return PT_OK;
@@ -927,7 +960,7 @@ int pt_check(const pt_scene* sc, void* stream) {
 
 int pt_inject_error(pt_scene* sc, int bits, void* stream) {
     if (!sc) return fail(PT_E_INVALID, "pt_inject_error: null scene");
-    if (bits <= 0 || bits > 7) return fail(PT_E_INVALID, "pt_inject_error: bits must be in 1..7");
+    if (bits <= 0 || bits > 15) return fail(PT_E_INVALID, "pt_inject_error: bits must be in 1..15");
     int h = 0;
     PT_CUDA(cudaMemcpyAsync(&h, sc->d_err, sizeof(int), cudaMemcpyDeviceToHost, S_(stream)));
     PT_CUDA(cudaStreamSynchronize(S_(stream)));

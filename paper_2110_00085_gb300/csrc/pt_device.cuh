@@ -25,7 +25,7 @@ constexpr uint32_t kKindScatter = 1u << 28;
 enum : uint32_t { kEndNone = 0, kEndEscape = 1, kEndTrunc = 2, kEndRR = 3, kEndMiss = 4 };
 
 // device-side error bits (pt_check)
-enum : int { kErrIndex = 1, kErrIter = 2, kErrRecord = 4 };
+enum : int { kErrIndex = 1, kErrIter = 2, kErrRecord = 4, kErrStore = 8 };
 
 struct DevCam {
     float C[3], F[3], R[3], U[3];

@@ -112,7 +112,13 @@ void launch_sample(const DevScene& S, const float* beta, uint64_t first, uint64_
 void launch_sort_count(const StoreBuf& in, uint64_t n, int n_buckets, uint32_t* blk_hist, Buckets* buckets,
                        cudaStream_t st);
 void launch_sort_scatter(const StoreBuf& in, uint64_t n, const uint32_t* blk_hist, Buckets* buckets, uint4* out_a,
-                         float4* out_b, cudaStream_t st);
+                         float4* out_b, cudaStream_t st, const uint32_t* abort = nullptr);
+// device-side fit check of a store that does not synchronise: an invalid
+// extinction grid (*bad != 0) or more records / events than the kept
+// buffers hold empties the bucket table, sets *abort and the error bit
+// kErrStore; else *abort = 0
+void launch_store_guard(Buckets* buckets, uint64_t rec_cap, uint64_t ev_cap, const uint32_t* bad, uint32_t* abort,
+                        int* err, cudaStream_t st);
 uint64_t sort_blocks(uint64_t n);   // blocks of the counting sort (rows of blk_hist)
 
 void launch_events(const DevScene& S, const SortedPaths& P, const Events& E, cudaStream_t st);

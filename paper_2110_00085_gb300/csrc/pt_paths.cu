@@ -96,7 +96,9 @@ __global__ void k_bucket_offsets(Buckets* bk, int n_buckets) {
 
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(StoreBuf in, uint64_t n, const uint32_t* __restrict__ blk_off,
                                                                uint32_t nblk, const Buckets* __restrict__ bk,
-                                                               uint4* __restrict__ out_a, float4* __restrict__ out_b) {
+                                                               uint4* __restrict__ out_a, float4* __restrict__ out_b,
+                                                               const uint32_t* __restrict__ abort) {
+    if (abort && *abort) return;   // block-uniform: the store did not fit (nothing is written)
     __shared__ uint32_t wc[kSortWarps][kBuckets];
     __shared__ uint32_t wp[kSortWarps][kBuckets];
     for (int k = threadIdx.x; k < kSortWarps * kBuckets; k += blockDim.x) (&wc[0][0])[k] = 0;
@@ -228,9 +230,31 @@ void launch_sort_count(const StoreBuf& in, uint64_t n, int n_buckets, uint32_t* 
 }
 
 void launch_sort_scatter(const StoreBuf& in, uint64_t n, const uint32_t* blk_hist, Buckets* buckets, uint4* out_a,
-                         float4* out_b, cudaStream_t st) {
+                         float4* out_b, cudaStream_t st, const uint32_t* abort) {
     const uint32_t nblk = blocks_for(n, kSortThreads);
-    k_sort_scatter<<<nblk, kSortThreads, 0, st>>>(in, n, blk_hist, nblk, buckets, out_a, out_b);
+    k_sort_scatter<<<nblk, kSortThreads, 0, st>>>(in, n, blk_hist, nblk, buckets, out_a, out_b, abort);
+}
+
+namespace {
+__global__ void k_store_guard(Buckets* bk, uint64_t rec_cap, uint64_t ev_cap, const uint32_t* bad, uint32_t* abort,
+                              int* err) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const bool fail = *bad != 0u || bk->rec_off[kBuckets] > rec_cap || bk->n_events > ev_cap;
+    *abort = fail ? 1u : 0u;
+    if (!fail) return;
+    for (int b = 0; b < kBuckets; ++b) bk->count[b] = 0;
+    for (int b = 0; b <= kBuckets; ++b) {
+        bk->path_off[b] = 0;
+        bk->rec_off[b] = 0;
+    }
+    bk->n_events = 0;
+    atomicOr(err, kErrStore);
+}
+}  // namespace
+
+void launch_store_guard(Buckets* buckets, uint64_t rec_cap, uint64_t ev_cap, const uint32_t* bad, uint32_t* abort,
+                        int* err, cudaStream_t st) {
+    k_store_guard<<<1, 32, 0, st>>>(buckets, rec_cap, ev_cap, bad, abort, err);
 }
 
 uint64_t sort_blocks(uint64_t n) { return blocks_for(n, kSortThreads); }

@@ -35,12 +35,21 @@ class ChunkedPaths:
     calls of native.Paths run chunk after chunk, the first writing the
     images / gradient and the others accumulating into them.  The Philox
     streams depend on the path id only, so the result is the single-handle
-    result up to the order of the FP64 additions."""
+    result up to the order of the FP64 additions.
 
-    def __init__(self, scene: N.Scene, chunk: int = MAX_CHUNK):
+    lean=True keeps one chunk's contribution cache at a time: a cached
+    reweight computes the images without the cache, and the gradient
+    reweights each chunk again with the cache (the same contributions),
+    takes its gradient and drops the cache -- one more forward pass per
+    step for a cache of one chunk instead of all (at workload 5: about
+    35 GB instead of 142 GB)."""
+
+    def __init__(self, scene: N.Scene, chunk: int = MAX_CHUNK, lean: bool = False):
         self.scene = scene
         self.chunk = int(chunk)
+        self.lean = bool(lean)
         self.parts = []
+        self._scratch = None
 
     def store(self, beta, n_paths: int, seed: int, epoch: int = 0, images_ref=None, tallies=None,
               fingerprints=None):
@@ -61,12 +70,20 @@ class ChunkedPaths:
         if images is None:
             images = self.scene.new_images()
         for i, p in enumerate(self.parts):
-            p.reweight(beta_t, images, cache=cache, accumulate=accumulate or i > 0)
+            p.reweight(beta_t, images, cache=cache and not self.lean, accumulate=accumulate or i > 0)
         return images
 
     def grad(self, beta_t, dldi, grad=None, cache: bool = False, accumulate: bool = False):
         if grad is None:
             grad = torch.zeros(self.scene.n_voxels, dtype=torch.float64, device=dldi.device)
+        if cache and self.lean:
+            if self._scratch is None:
+                self._scratch = self.scene.new_images()
+            for i, p in enumerate(self.parts):
+                p.reweight(beta_t, self._scratch, cache=True)
+                p.grad(beta_t, dldi, grad, cache=True, accumulate=accumulate or i > 0)
+                p.drop_cache()
+            return grad
         for i, p in enumerate(self.parts):
             p.grad(beta_t, dldi, grad, cache=cache, accumulate=accumulate or i > 0)
         return grad
@@ -107,7 +124,8 @@ class Reconstruction:
 
     def __init__(self, scene: N.Scene, gt_images: torch.Tensor, beta0: torch.Tensor, n_paths: int,
                  n_r: int = 10, lr: float = 1.0, seed: int = 1234, cache: bool = True,
-                 b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8, decorrelate: bool = False):
+                 b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8, decorrelate: bool = False,
+                 lean: bool = False):
         self.scene = scene
         self.gt = gt_images
         self.beta = beta0.clone().contiguous()
@@ -121,7 +139,7 @@ class Reconstruction:
         self.decorrelate = bool(decorrelate)
         # one handle up to MAX_CHUNK paths, chunked handles above
         per_set = self.n_paths // 2 if self.decorrelate else self.n_paths
-        make = (lambda: N.Paths(scene)) if per_set <= MAX_CHUNK else (lambda: ChunkedPaths(scene))
+        make = (lambda: N.Paths(scene)) if per_set <= MAX_CHUNK else (lambda: ChunkedPaths(scene, lean=lean))
         self.paths = make()
         self.paths_b = make() if self.decorrelate else None
         self.images = scene.new_images()
@@ -186,7 +204,8 @@ class Reconstruction:
             timers.setdefault("render_grad", []).append((a, ev()))
         N.adam_step(self.beta, self.m, self.v, self.grad, self.t + 1, self.lr, self.b1, self.b2, self.eps,
                     mask=self.mask)
-        self.launches += self._parts() * (LAUNCHES["reweight"] + (
+        lean = isinstance(self.paths, ChunkedPaths) and self.paths.lean and self.cache
+        self.launches += self._parts() * ((2 if lean else 1) * LAUNCHES["reweight"] + (
             LAUNCHES["grad_cache"] if self.cache else LAUNCHES["grad"])) + LAUNCHES["residual"] * (
             2 if self.decorrelate else 1) + LAUNCHES["adam"]
         self.t += 1

@@ -20,6 +20,7 @@ from . import build as _build
 PT_ACCUMULATE = 1
 PT_CACHE = 2
 PT_SORT = 4
+PT_ASYNC = 8
 TALLY_NAMES = ["injected", "missed", "escaped", "absorbed", "truncated", "rr_killed",
                "rr_gain", "collisions", "entered", "seg_cross", "shadow_cross", "in_view"]
 TALLY_COUNT = len(TALLY_NAMES)
@@ -80,6 +81,7 @@ def load():
         L.render_grad.argtypes = [_vp, _vp, _vp, _vp, _u32, _vp]
         L.paths_free.argtypes = [_vp]
         L.paths_cache_token.argtypes = [_vp]
+        L.paths_drop_cache.argtypes = [_vp]
         L.paths_cache_token.restype = _u64
         L.paths_info.argtypes = [_vp, C.POINTER(PtPathsInfo), _vp]
         L.adam_step.argtypes = [_vp, _vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.c_float, C.c_float, C.c_float,
@@ -235,13 +237,18 @@ class Paths:
 
     def store(self, beta: torch.Tensor, n_paths: int, seed: int, first: int = 0, n_norm=None, epoch: int = 0,
               images_ref: Optional[torch.Tensor] = None, accumulate: bool = False,
-              tallies: Optional[torch.Tensor] = None, fingerprints: Optional[torch.Tensor] = None, stream=None):
+              tallies: Optional[torch.Tensor] = None, fingerprints: Optional[torch.Tensor] = None, stream=None,
+              asynchronous: bool = False):
+        """``asynchronous``: PT_ASYNC (no stream synchronisation on a handle an
+        earlier store has sized; a set that does not fit, or an invalid
+        grid, is reported by Scene.check())."""
         n_norm = float(n_paths if n_norm is None else n_norm)
         sc = self.scene
+        flags = (PT_ACCUMULATE if accumulate else 0) | (PT_ASYNC if asynchronous else 0)
         rc = load().paths_store(sc.handle, _dev(beta, torch.float32, "beta", sc.n_voxels), first, n_paths, n_norm,
                                 seed, epoch, C.byref(self._h),
                                 _opt(images_ref, torch.float64, "images_ref", sc.n_pixels),
-                                PT_ACCUMULATE if accumulate else 0,
+                                flags,
                                 _opt(tallies, torch.float64, "tallies", TALLY_COUNT),
                                 _opt(fingerprints, torch.int64, "fingerprints", n_paths),
                                 _vp(_stream(stream)))
@@ -271,6 +278,10 @@ class Paths:
                                 _dev(grad, torch.float64, "grad", sc.n_voxels), flags, _vp(_stream(stream)))
         _check(rc, "render_grad")
         return grad
+
+    def drop_cache(self):
+        """Free the contribution cache (the next cached reweight allocates it again)."""
+        _check(load().paths_drop_cache(self._h), "paths_drop_cache")
 
     def cache_token(self) -> int:
         """Which cache-writing reweight the contribution cache holds (0: none)."""

@@ -280,6 +280,85 @@ def test_store_rejects_invalid_extinction_before_tracing():
     scene.check()
 
 
+def test_async_store_equals_synchronous_store():
+    """paths_store(PT_ASYNC) on a handle that a synchronous store has sized
+    stores the same paths as a synchronous store (images and gradient equal
+    to FP64 summation order) without synchronising."""
+    sc = synth.config(1, n_paths=1 << 14)
+    scene = N.Scene(sc)
+    b = t32(sc.beta_cloud)
+    bt = t32(_perturbed(sc.beta_cloud, 8))
+    A = N.Paths(scene).store(b, sc.n_paths, sc.seed, epoch=0)
+    A.store(b, sc.n_paths, sc.seed, epoch=1, asynchronous=True)
+    ia = A.reweight(bt, cache=True)
+    dl = ia - 0.5 * ia.mean()
+    ga = A.grad(bt, dl, cache=True)
+    B = N.Paths(scene).store(b, sc.n_paths, sc.seed, epoch=1)
+    ib = B.reweight(bt, cache=True)
+    gb = B.grad(bt, dl, cache=True)
+    torch.cuda.synchronize()
+    scene.check()
+    assert float(ib.sum()) > 0
+    assert torch.allclose(ia, ib, rtol=1e-12, atol=0)
+    assert float((ga - gb).abs().sum()) <= 1e-9 * float(gb.abs().sum())
+    assert A.info()["n_stored"] == B.info()["n_stored"]
+    A.close()
+    B.close()
+
+
+def test_async_store_reports_what_it_cannot_hold():
+    """A PT_ASYNC store of an invalid grid, or of more records than the
+    handle's buffers hold, leaves the handle without paths (later passes add
+    nothing) and is reported by pt_check (bit 8); a synchronous store then
+    grows the buffers and works."""
+    sc = synth.config(1, n_paths=1 << 10)
+    scene = N.Scene(sc)
+    good = t32(sc.beta_cloud)
+    P = N.Paths(scene).store(good, 1 << 10, 1)
+    bad = good.clone()
+    bad[[3, 9]] = float("nan")
+    P.store(bad, 1 << 10, 1, asynchronous=True)
+    assert float(P.reweight(good).abs().sum()) == 0.0
+    with pytest.raises(RuntimeError, match="0x8"):
+        scene.check()
+    P.store(good, 1 << 14, 2, asynchronous=True)   # about 16x the records the buffers hold
+    assert float(P.reweight(good).abs().sum()) == 0.0
+    assert P.info()["n_stored"] == 0
+    with pytest.raises(RuntimeError, match="0x8"):
+        scene.check()
+    P.store(good, 1 << 14, 2)
+    assert float(P.reweight(good).sum()) > 0
+    scene.check()
+    P.close()
+
+
+def test_lean_chunked_cache_equals_full_cache():
+    """A path set in four handles, keeping one handle's contribution cache at
+    a time (reweight without the cache, then per handle reweight with it,
+    gradient, drop): the same images and gradient as with every cache kept,
+    and the caches are freed."""
+    from paper_2110_00085_gb300.driver import ChunkedPaths
+    sc = synth.config(1, n_paths=1 << 14)
+    scene = N.Scene(sc)
+    b = t32(sc.beta_cloud)
+    bt = t32(_perturbed(sc.beta_cloud, 9))
+    full = ChunkedPaths(scene, chunk=1 << 12).store(b, sc.n_paths, sc.seed)
+    lean = ChunkedPaths(scene, chunk=1 << 12, lean=True).store(b, sc.n_paths, sc.seed)
+    assert len(full.parts) == 4 and len(lean.parts) == 4
+    i1 = full.reweight(bt, cache=True)
+    dl = i1 - 0.5 * i1.mean()
+    g1 = full.grad(bt, dl, cache=True)
+    i2 = lean.reweight(bt, cache=True)
+    g2 = lean.grad(bt, dl, cache=True)
+    torch.cuda.synchronize()
+    scene.check()
+    assert torch.allclose(i1, i2, rtol=1e-12, atol=0)
+    assert float((g1 - g2).abs().sum()) <= 1e-9 * float(g1.abs().sum())
+    assert lean.info()["bytes_device"] < full.info()["bytes_device"]
+    full.close()
+    lean.close()
+
+
 def test_repeated_passes_agree_to_summation_order():
     """Determinism: the same recycled forward and gradient run twice on the
     same stored paths agree to FP64 summation-order noise (the atomics'
