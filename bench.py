@@ -774,7 +774,7 @@ def run_surfaces(args, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
-def rooflines(avg, dom, T, info, n, n_cams, probes, dev):
+def rooflines(avg, dom, T, info, n, n_cams, probes, dev, lean=False):
     """Achieved rates of the passes against the measured peaks.
 
     Algorithmic work per call, from the tallies of the stored path set:
@@ -854,6 +854,11 @@ def rooflines(avg, dom, T, info, n, n_cams, probes, dev):
         main["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernels at 2^20 "
                                   "paths (profiles/traffic_render_grad_noise128.txt), scaled by paths")
     main["hbm_peak_source"] = f"{pk_src} ({'MEASURED_PEAKS.json' if pk_src == 'measured' else 'fallback'})"
+    if lean:
+        # one chunk's contribution cache at a time: render_grad re-runs each
+        # chunk's forward pass before its gradient, inside the timed call
+        main["note"] = ("lean cache: the render_grad time includes a forward pass per chunk, so the fraction "
+                        "understates the gradient kernel's own rate")
     return {"main": main, "views": views}
 
 
@@ -987,7 +992,8 @@ def run_native(args, ws, rank, local):
     amortized = (avg.get("paths_store", 0.0) / N_R + avg.get("paths_reweight", 0.0) + avg.get("render_grad", 0.0)
                  + max(other, 0.0))
     dom = max(tot, key=tot.get)
-    roof = rooflines(avg, dom, T, info, n, len(sc.cameras), probes, dev)
+    roof = rooflines(avg, dom, T, info, n, len(sc.cameras), probes, dev,
+                     lean=bool(args.lean and n > (1 << 26)))
 
     # ---- the recycling ablation (norm-free): Alg. 2 vs Alg. 1 in time ----
     abl = None
