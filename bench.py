@@ -868,7 +868,7 @@ def run_native(args, ws, rank, local):
     import __graft_entry__ as G
     G.build()
     from paper_2110_00085_gb300 import native as N
-    from paper_2110_00085_gb300.driver import Reconstruction
+    from paper_2110_00085_gb300.driver import Reconstruction, ShardedReconstruction
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -876,7 +876,16 @@ def run_native(args, ws, rank, local):
     probes = measure_peaks(dev)
     sc, gt_np, beta0_np = workload(args.paths, args.workload)
     n = sc.n_paths
-    scene = N.Scene(sc, scene_id=rank)
+    # --shard: one optimisation over ws x n paths, each rank holding n of them
+    # (the same scene and streams on every rank; images and gradient summed
+    # over the ranks by NCCL); otherwise ws independent replicas
+    shard = args.shard and ws > 1
+    group = None
+    if shard:
+        import torch.distributed as td
+        group = td.new_group(backend="nccl")
+    scene = N.Scene(sc, scene_id=0 if shard else rank)
+    seed = sc.seed if shard else sc.seed + rank
     beta_gt = torch.from_numpy(gt_np.reshape(-1)).to(dev)
     beta0 = torch.from_numpy(beta0_np.reshape(-1)).to(dev)
     # ground-truth images: independent seed, 4x the path budget (not timed;
@@ -890,12 +899,14 @@ def run_native(args, ws, rank, local):
     lr = float(gt_np.max()) / 50.0
 
     def make(n_r):
-        return Reconstruction(scene, gt_img, beta0, n, n_r=n_r, lr=lr, seed=sc.seed + rank, cache=True,
-                              lean=args.lean)
+        if shard:
+            return ShardedReconstruction(scene, gt_img, beta0, ws * n, group=group, n_r=n_r, lr=lr, seed=seed,
+                                         cache=True, lean=args.lean)
+        return Reconstruction(scene, gt_img, beta0, n, n_r=n_r, lr=lr, seed=seed, cache=True, lean=args.lean)
 
     # ---- algorithmic work per pass: voxel crossings of the stored paths ----
     tal = torch.zeros(N.TALLY_COUNT, dtype=torch.float64, device=dev)
-    scene.render_forward(beta0, n, sc.seed + rank, tallies=tal)
+    scene.render_forward(beta0, n, seed, first=rank * n if shard else 0, tallies=tal)
     T = dict(zip(N.TALLY_NAMES, tal.cpu().numpy().tolist()))
 
     # ---- reuse arm (Alg. 2): warm-up, then K timed steps ----
@@ -955,10 +966,11 @@ def run_native(args, ws, rank, local):
     # ---- matched gradient error: reuse at n vs resample at n* ----
     # (above 2^26 paths the reference gradients of 4N paths and the
     # ablation's 2 x 50 steps take too long for one run: not measured there)
-    heavy = not args.no_calibration and n <= (1 << 26)
+    # (sharded runs: not measured, the arms are single-process)
+    heavy = not args.no_calibration and n <= (1 << 26) and not shard
     matched = None
     if heavy:
-        matched = calibrate_matched(args, ws, scene, gt_img, beta0, n, lr, sc.seed + rank, ms)
+        matched = calibrate_matched(args, ws, scene, gt_img, beta0, n, lr, seed, ms)
 
     # ---- end to end through the public API with host buffers ----
     gt_host = gt_img.cpu().pin_memory()
@@ -998,7 +1010,7 @@ def run_native(args, ws, rank, local):
     # ---- the recycling ablation (norm-free): Alg. 2 vs Alg. 1 in time ----
     abl = None
     if heavy:
-        abl = ablation(args, ws, scene, gt_img, beta_gt, beta0, n, lr, sc.seed + rank, steps=args.ablation_steps)
+        abl = ablation(args, ws, scene, gt_img, beta_gt, beta0, n, lr, seed, steps=args.ablation_steps)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -1013,7 +1025,9 @@ def run_native(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": CONFIGS[args.workload][1], "n_paths": n, "n_r": N_R, "replicas": ws,
+        "config": {"workload": CONFIGS[args.workload][1], "n_paths": n, "n_r": N_R,
+                   "parallelism": (f"paths sharded over {ws} ranks ({ws * n} paths per optimisation, NCCL "
+                                   "all-reduce of images and gradient)") if shard else f"{ws} independent replicas",
                    "lean_cache": bool(args.lean and n > (1 << 26)),
                    "accumulation": "f64 pixel and gradient sums",
                    "l2": "inputs larger than L2 (stored paths and contribution cache, GBs per step)",
@@ -1068,6 +1082,9 @@ def main():
     ap.add_argument("--recon-snr", action="store_true",
                     help="recon workload: first measure the start state's gradient cosine to a reference")
     ap.add_argument("--path-scale", type=int, default=0, help="batch workload: lower every 2^k path budget by k")
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: split one optimisation's paths over the ranks (n paths per rank) instead of "
+                         "running independent replicas")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":

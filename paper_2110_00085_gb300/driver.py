@@ -52,18 +52,21 @@ class ChunkedPaths:
         self._scratch = None
 
     def store(self, beta, n_paths: int, seed: int, epoch: int = 0, images_ref=None, tallies=None,
-              fingerprints=None):
+              fingerprints=None, first: int = 0, n_norm=None):
+        """Paths [first, first + n_paths), normalised by n_norm (default n_paths)."""
         n = int(n_paths)
+        norm = n if n_norm is None else n_norm
         k = (n + self.chunk - 1) // self.chunk
         while len(self.parts) < k:
             self.parts.append(N.Paths(self.scene))
         while len(self.parts) > k:
             self.parts.pop().close()
         for i, p in enumerate(self.parts):
-            first = i * self.chunk
-            m = min(self.chunk, n - first)
-            p.store(beta, m, seed, first=first, n_norm=n, epoch=epoch, images_ref=images_ref, accumulate=i > 0,
-                    tallies=tallies, fingerprints=None if fingerprints is None else fingerprints[first:first + m])
+            off = i * self.chunk
+            m = min(self.chunk, n - off)
+            p.store(beta, m, seed, first=int(first) + off, n_norm=norm, epoch=epoch, images_ref=images_ref,
+                    accumulate=i > 0, tallies=tallies,
+                    fingerprints=None if fingerprints is None else fingerprints[off:off + m])
         return self
 
     def reweight(self, beta_t, images=None, cache: bool = False, accumulate: bool = False):
@@ -138,7 +141,7 @@ class Reconstruction:
         self.cache = cache
         self.decorrelate = bool(decorrelate)
         # one handle up to MAX_CHUNK paths, chunked handles above
-        per_set = self.n_paths // 2 if self.decorrelate else self.n_paths
+        per_set = max(count for _, count, _ in self._sets())
         make = (lambda: N.Paths(scene)) if per_set <= MAX_CHUNK else (lambda: ChunkedPaths(scene, lean=lean))
         self.paths = make()
         self.paths_b = make() if self.decorrelate else None
@@ -155,15 +158,27 @@ class Reconstruction:
         self.launches = 0
         self.mask = None     # optional uint8 voxel mask: voxels with 0 are not optimised
 
-    def resample(self):
+    def _sets(self):
+        """(first id, count, normaliser) of each path set this process stores:
+        the whole budget, or its halves A and B when decorrelated."""
         if self.decorrelate:
             h = self.n_paths // 2
-            self.paths.store(self.beta, h, self.seed, epoch=self.epoch)
-            self.paths_b.store(self.beta, h, self.seed, first=h, epoch=self.epoch)
-        else:
-            self.paths.store(self.beta, self.n_paths, self.seed, epoch=self.epoch)
+            return [(0, h, h), (h, h, h)]
+        return [(0, self.n_paths, self.n_paths)]
+
+    def resample(self):
+        for handle, (first, count, norm) in zip((self.paths, self.paths_b), self._sets()):
+            handle.store(self.beta, count, self.seed, first=first, n_norm=norm, epoch=self.epoch)
         self.epoch += 1
         self.launches += LAUNCHES["store"] * self._parts()
+
+    # the images and the gradient of this process's paths are the whole
+    # estimate here; ShardedReconstruction sums them over its ranks
+    def _combine_images(self):
+        pass
+
+    def _combine_grad(self):
+        pass
 
     def _parts(self) -> int:
         k = len(self.paths.parts) if isinstance(self.paths, ChunkedPaths) else 1
@@ -187,6 +202,7 @@ class Reconstruction:
         self.paths.reweight(self.beta, self.images, cache=self.cache)
         if self.decorrelate:
             self.paths_b.reweight(self.beta, self.images_b, cache=self.cache)
+        self._combine_images()
         if timers is not None:
             timers.setdefault("paths_reweight", []).append((a, ev()))
         N.loss_residual(self.images, self.gt, self.dldi, self.loss)
@@ -200,6 +216,7 @@ class Reconstruction:
             self.loss.add_(self.loss_b).mul_(0.5)
         else:
             self.paths.grad(self.beta, self.dldi, self.grad, cache=self.cache)
+        self._combine_grad()
         if timers is not None:
             timers.setdefault("render_grad", []).append((a, ev()))
         N.adam_step(self.beta, self.m, self.v, self.grad, self.t + 1, self.lr, self.b1, self.b2, self.eps,
@@ -254,6 +271,74 @@ class Reconstruction:
         self.paths.close()
         if self.paths_b is not None:
             self.paths_b.close()
+
+
+def shard_range(n_paths: int, rank: int, world: int):
+    """The contiguous path ids [first, first + count) of one rank when a set of
+    n_paths paths is split over `world` ranks: shares differ by at most one
+    path, the first n_paths mod world ranks take the larger ones, and the
+    ranges tile [0, n_paths) in rank order.  Paths are independent (Sec. 5.3),
+    and each path's random stream depends on its id only, so the union of the
+    shards is the same path set as one process's."""
+    n, r, w = int(n_paths), int(rank), int(world)
+    if w < 1 or not 0 <= r < w or n < 0:
+        raise ValueError(f"shard_range: rank {r} of world {w}, {n} paths")
+    base, extra = divmod(n, w)
+    return r * base + min(r, extra), base + (1 if r < extra else 0)
+
+
+def allreduce_sum(t: torch.Tensor, group=None) -> torch.Tensor:
+    """Sum a tensor over the ranks of a process group, in place (NCCL on GPUs;
+    gloo also takes CUDA tensors).  Every rank receives the same bits."""
+    import torch.distributed as td
+    td.all_reduce(t, op=td.ReduceOp.SUM, group=group)
+    return t
+
+
+class ShardedReconstruction(Reconstruction):
+    """Alg. 2 with the path budget split over the ranks of a process group,
+    one GPU per rank.  Each rank stores the ids shard_range gives it of every
+    path set, normalised by the set's total, so its images and gradient are
+    its part of the sums over paths (Eq. 19 and Eq. 21 are sums over
+    independent paths).  A step is then:
+      paths_reweight on the rank's paths       partial images
+      all-reduce of the FP64 images            the whole estimate F
+      loss_residual(F, I_gt)                   the same dL/dI on every rank
+      render_grad on the rank's paths          partial gradient
+      all-reduce of the FP64 gradient          the whole gradient
+      adam_step                                the same extinction on every rank
+    The two all-reduces are the only exchange: the extinction, the Adam
+    moments and the residual stay replicated, and every rank applies the same
+    update to the same bits.  With one rank it is Reconstruction."""
+
+    def __init__(self, scene: N.Scene, gt_images: torch.Tensor, beta0: torch.Tensor, n_paths: int, group=None,
+                 **kw):
+        import torch.distributed as td
+        self.group = group
+        self.rank = td.get_rank(group) if td.is_initialized() else 0
+        self.world = td.get_world_size(group) if td.is_initialized() else 1
+        half = int(n_paths) // 2 if kw.get("decorrelate") else int(n_paths)
+        if half < self.world:
+            raise ValueError(f"ShardedReconstruction: {half} paths per set cannot give each of {self.world} "
+                             "ranks at least one")
+        super().__init__(scene, gt_images, beta0, n_paths, **kw)
+
+    def _sets(self):
+        out = []
+        for first, count, norm in super()._sets():
+            f, c = shard_range(count, self.rank, self.world)
+            out.append((first + f, c, norm))
+        return out
+
+    def _combine_images(self):
+        if self.world > 1:
+            allreduce_sum(self.images, self.group)
+            if self.decorrelate:
+                allreduce_sum(self.images_b, self.group)
+
+    def _combine_grad(self):
+        if self.world > 1:
+            allreduce_sum(self.grad, self.group)
 
 
 class BatchReconstruction:
