@@ -883,7 +883,7 @@ def run_native(args, ws, rank, local):
     group = None
     if shard:
         import torch.distributed as td
-        group = td.new_group(backend="nccl")
+        group = td.new_group(backend=args.shard_backend)
     scene = N.Scene(sc, scene_id=0 if shard else rank)
     seed = sc.seed if shard else sc.seed + rank
     beta_gt = torch.from_numpy(gt_np.reshape(-1)).to(dev)
@@ -1026,8 +1026,9 @@ def run_native(args, ws, rank, local):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": CONFIGS[args.workload][1], "n_paths": n, "n_r": N_R,
-                   "parallelism": (f"paths sharded over {ws} ranks ({ws * n} paths per optimisation, NCCL "
-                                   "all-reduce of images and gradient)") if shard else f"{ws} independent replicas",
+                   "parallelism": (f"paths sharded over {ws} ranks ({ws * n} paths per optimisation, "
+                                   f"{args.shard_backend} all-reduce of images and gradient)") if shard
+                                  else f"{ws} independent replicas",
                    "lean_cache": bool(args.lean and n > (1 << 26)),
                    "accumulation": "f64 pixel and gradient sums",
                    "l2": "inputs larger than L2 (stored paths and contribution cache, GBs per step)",
@@ -1085,6 +1086,8 @@ def main():
     ap.add_argument("--shard", action="store_true",
                     help="N > 1: split one optimisation's paths over the ranks (n paths per rank) instead of "
                          "running independent replicas")
+    ap.add_argument("--shard-backend", default="nccl", choices=["nccl", "gloo"],
+                    help="--shard: the process group that sums images and gradient")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":

@@ -116,3 +116,37 @@ def test_sharded_adam_step_moves_the_extinction_like_one_process():
     assert firm.sum() > 1000
     assert np.allclose(b2[firm], b1[firm], rtol=1e-6, atol=1e-6)
     assert np.abs(b1 - 0.8 * synth.config(1).beta_cloud.reshape(-1)).max() > 0.1
+
+
+def _bench_rank(rank, world, port, out):
+    import contextlib
+    import io
+    import sys
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK="0")
+    import bench
+    sys.argv = ["bench.py", "--gpus", str(world), "--steps", "2", "--warmup", "1", "--paths", str(1 << 16),
+                "--no-cpu", "--no-calibration", "--shard", "--shard-backend", "gloo"]
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.main()
+    out[rank] = buf.getvalue()
+
+
+def test_bench_sharded_path_runs_on_two_ranks():
+    """bench.py --shard end to end: two ranks (processes on this one GPU,
+    gloo in place of NCCL, which needs a GPU per rank) time one optimisation
+    of 2 x 2^16 paths; rank 0 prints the line, which counts every rank's
+    paths and names the sharding."""
+    import json
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_bench_rank, args=(world, _free_port(), out), nprocs=world, start_method="spawn", join=True)
+    lines = [l for l in out[0].splitlines() if l.startswith("{")]
+    assert len(lines) == 1 and not [l for l in out[1].splitlines() if l.startswith("{")]
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == world and d["config"]["n_paths"] == 1 << 16
+    assert "sharded over 2 ranks" in d["config"]["parallelism"]
+    assert d["value"] == pytest.approx(world * (1 << 16) / (d["ms_per_step"] * 1e-3), rel=1e-9)
+    assert d["gpu_launches"] > 0 and d["matched_error"] is None
