@@ -562,8 +562,7 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
     // the scatter.  The kept arrays are sized from the actual record and
     // event counts, read once the counting sort has run.
     StoreBuf sbuf{nullptr, nullptr, nullptr, n};
-    uint32_t* blk = nullptr;
-    const uint64_t nblk = sort_blocks(n);
+    uint32_t* sortw = nullptr;
     cudaMemPool_t pool = store_pool();
     auto tmp = [&](void** q, uint64_t bytes, const char* what) -> int {
         const cudaError_t e = pool ? cudaMallocFromPoolAsync(q, bytes ? bytes : 16, pool, st)
@@ -576,13 +575,13 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
         return PT_OK;
     };
     auto release = [&]() {
-        for (void* q : {(void*)sbuf.rec_a, (void*)sbuf.rec_b, (void*)sbuf.cnt, (void*)blk})
+        for (void* q : {(void*)sbuf.rec_a, (void*)sbuf.rec_b, (void*)sbuf.cnt, (void*)sortw})
             if (q) cudaFreeAsync(q, st);
     };
     if ((rc = tmp((void**)&sbuf.rec_a, sizeof(uint4) * n * slots, "sampled records A")) ||
         (rc = tmp((void**)&sbuf.rec_b, sizeof(float4) * n * slots, "sampled records B")) ||
         (rc = tmp((void**)&sbuf.cnt, sizeof(uint8_t) * n, "collision counts")) ||
-        (rc = tmp((void**)&blk, sizeof(uint32_t) * nblk * kBuckets, "block histogram"))) {
+        (rc = tmp((void**)&sortw, sizeof(uint32_t) * sort_scratch_words(n), "path sort keys and bins"))) {
         release();
         return rc;
     }
@@ -591,11 +590,14 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
     // without images_ref the kernel traces flights only (no shadow rays)
     launch_sample(sc->ds, beta, first, n, p->inv_norm, seed, epoch, images_ref, tallies, fps, &sbuf, st);
     if ((rc = launch_status("paths_store"))) { release(); return rc; }
-    launch_sort_count(sbuf, n, slots, blk, p->bk, st);
+    // Morton bins of the first collision: the grid's Morton code reduced to 12 bits
+    const SortScratch sw = sort_scratch(sortw, n);
+    const int key_shift = std::max(0, 3 * event_bin_bits(sc->ds) - 12);
+    launch_sort_count(sbuf, n, slots, key_shift, sw, p->bk, st);
     if ((rc = launch_status("paths_store sort"))) { release(); return rc; }
     if (async) {
         launch_store_guard(p->bk, p->rec_cap, p->ev.cap, p->bad, p->abort_flag, sc->d_err, st);
-        launch_sort_scatter(sbuf, n, blk, p->bk, p->sa, p->sb, st, p->abort_flag);
+        launch_sort_scatter(sbuf, n, sw, p->bk, p->sa, p->sb, st, p->abort_flag);
         release();
         if ((rc = launch_status("paths_store sort"))) return rc;
         launch_events(sc->ds, sorted_view(p), p->ev, st);
@@ -639,7 +641,7 @@ int paths_store(const pt_scene* sc, const float* beta, uint64_t first, uint64_t 
         }
         E.cap = c;
     }
-    launch_sort_scatter(sbuf, n, blk, p->bk, p->sa, p->sb, st);
+    launch_sort_scatter(sbuf, n, sw, p->bk, p->sa, p->sb, st);
     release();
     if ((rc = launch_status("paths_store sort"))) return rc;
     launch_events(sc->ds, sorted_view(p), p->ev, st);

@@ -147,15 +147,20 @@ unsigned blocks(uint64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace
 
+void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n, cudaStream_t st) {
+    if (n == 0) return;
+    const uint32_t nb = (n + kScanItems - 1) / kScanItems;   // <= 4096 for n <= 2^24
+    k_scan_blocks<<<nb, 1024, 0, st>>>(in, out, partial, n);
+    k_scan_blocks<<<1, 1024, 0, st>>>(partial, partial + kScanItems, partial + 2 * kScanItems, nb);
+    k_scan_add<<<nb, 1024, 0, st>>>(out, partial + kScanItems, n);
+}
+
 void launch_events(const DevScene& S, const SortedPaths& P, const Events& E, cudaStream_t st) {
     const unsigned g = blocks(P.n_max, 128);
     if (g == 0) return;
     cudaMemsetAsync(E.hist, 0, sizeof(uint32_t) * E.n_bins, st);
     k_ev_hist<<<g, 128, 0, st>>>(S, P, E);
-    const uint32_t nb = (E.n_bins + kScanItems - 1) / kScanItems;   // <= 4096 for 2^24 bins
-    k_scan_blocks<<<nb, 1024, 0, st>>>(E.hist, E.cursor, E.partial, E.n_bins);
-    k_scan_blocks<<<1, 1024, 0, st>>>(E.partial, E.partial + kScanItems, E.partial + 2 * kScanItems, nb);
-    k_scan_add<<<nb, 1024, 0, st>>>(E.cursor, E.partial + kScanItems, E.n_bins);
+    launch_scan(E.hist, E.cursor, E.partial, E.n_bins, st);
     k_ev_scatter<<<g, 128, 0, st>>>(S, P, E);
 }
 

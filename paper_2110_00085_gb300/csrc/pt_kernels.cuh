@@ -106,20 +106,34 @@ void launch_sample(const DevScene& S, const float* beta, uint64_t first, uint64_
                    uint32_t epoch, double* images, double* tallies, uint64_t* fps, const StoreBuf* store,
                    cudaStream_t st);
 
-// counting sort of the stored paths by collision count: counts and bucket
-// offsets (readable from `buckets` when the stream reaches this point), then
-// the scatter of the records into bucket-contiguous order
-void launch_sort_count(const StoreBuf& in, uint64_t n, int n_buckets, uint32_t* blk_hist, Buckets* buckets,
-                       cudaStream_t st);
-void launch_sort_scatter(const StoreBuf& in, uint64_t n, const uint32_t* blk_hist, Buckets* buckets, uint4* out_a,
+// counting sort of the stored paths by collision count and, inside a
+// count, by the Morton code of the first collision's voxel (kPathBins bins):
+// keys, counts and bucket offsets (readable from `buckets` when the stream
+// reaches this point), then the scatter of the records into bucket-
+// contiguous order.  Scratch: sort_scratch_words(n) 32-bit words.
+constexpr uint32_t kPathBins = 4096;
+constexpr uint32_t kSortBins = kBuckets * kPathBins;
+struct SortScratch {
+    uint32_t* keys;      // n
+    uint32_t* hist;      // kSortBins
+    uint32_t* cursor;    // kSortBins
+    uint32_t* partial;   // 3 x 4096 (scan)
+    uint32_t* n_zero;    // 1: paths without a collision
+};
+uint64_t sort_scratch_words(uint64_t n);
+SortScratch sort_scratch(uint32_t* base, uint64_t n);
+void launch_sort_count(const StoreBuf& in, uint64_t n, int n_buckets, int key_shift, const SortScratch& w,
+                       Buckets* buckets, cudaStream_t st);
+void launch_sort_scatter(const StoreBuf& in, uint64_t n, const SortScratch& w, Buckets* buckets, uint4* out_a,
                          float4* out_b, cudaStream_t st, const uint32_t* abort = nullptr);
+// exclusive scan of n <= 2^24 counts (in -> out); partial: 3 x 4096 words
+void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n, cudaStream_t st);
 // device-side fit check of a store that does not synchronise: an invalid
 // extinction grid (*bad != 0) or more records / events than the kept
 // buffers hold empties the bucket table, sets *abort and the error bit
 // kErrStore; else *abort = 0
 void launch_store_guard(Buckets* buckets, uint64_t rec_cap, uint64_t ev_cap, const uint32_t* bad, uint32_t* abort,
                         int* err, cudaStream_t st);
-uint64_t sort_blocks(uint64_t n);   // blocks of the counting sort (rows of blk_hist)
 
 void launch_events(const DevScene& S, const SortedPaths& P, const Events& E, cudaStream_t st);
 

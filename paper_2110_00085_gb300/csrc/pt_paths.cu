@@ -1,10 +1,12 @@
 // pt_paths.cu -- stored light paths: the path sort (Sec. 5.3), the recycled
 // forward pass and the gradient pass over sorted paths (Sec. 5.2, Sec. 4.4).
 //
-// Sort: stable counting sort of paths by their number of collisions B
-// (histogram per block -> per-bucket scan over blocks -> scatter), so that
-// the 32 lanes of a warp always hold paths of equal size (the paper's path
-// sorting, which lets every lane run the same number of events).
+// Sort: counting sort of paths by their number of collisions B (the paper's
+// path sorting: the 32 lanes of a warp hold paths of equal size, so every
+// lane runs the same number of events) and, inside a size, by the Morton
+// code of the voxel of the first collision (4096 bins of the grid), so that
+// a warp's paths also start their walks close together: key histogram ->
+// scan -> scatter.
 //
 // Recycled forward (Eq. forward_simualtion_recycling): for each stored event
 // b the contribution under the current extinction M_t, times the correction
@@ -17,72 +19,51 @@
 // the vertex adds a * h(x_b, mu_bd); per flight k the suffix sum
 // S_k = sum_{b >= k} A_b scatters -S_k * l_v and vertex k adds
 // h(x_k, mu_k) * S_{k+1}, with h = albedo_c f^c / f_s.
-#include "pt_kernels.cuh"
+#include "pt_event_ops.cuh"
 
 namespace pt {
 
 namespace {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortWarps = kSortThreads / 32;
+constexpr uint32_t kNoKey = 0xffffffffu;
 
 // ------------------------------------------------------------ sort ------
-__device__ __forceinline__ void warp_bucket_counts(uint32_t b, uint32_t (*wc)[kBuckets], uint32_t& rank) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t peers = __match_any_sync(0xffffffffu, b);
-    rank = __popc(peers & ((1u << lane) - 1u));
-    if (lane == __ffs(peers) - 1 && b < (uint32_t)kBuckets) wc[warp][b] = __popc(peers);
-}
-
-__global__ void __launch_bounds__(kSortThreads) k_sort_count(const uint8_t* __restrict__ cnt, uint64_t n,
-                                                             uint32_t* __restrict__ blk_hist, uint32_t nblk) {
-    __shared__ uint32_t wc[kSortWarps][kBuckets];
-    for (int k = threadIdx.x; k < kSortWarps * kBuckets; k += blockDim.x) (&wc[0][0])[k] = 0;
-    __syncthreads();
+// key of path i: its size B (1 .. n_buckets - 1) times kPathBins plus the
+// Morton code of its first collision's voxel >> key_shift; kNoKey for a path
+// that is not stored (B = 0)
+__global__ void __launch_bounds__(kSortThreads) k_sort_keys(StoreBuf in, uint64_t n, int n_buckets, int key_shift,
+                                                            uint32_t* __restrict__ keys, uint32_t* __restrict__ hist,
+                                                            uint32_t* __restrict__ n_zero) {
     const uint64_t i = (uint64_t)blockIdx.x * kSortThreads + threadIdx.x;
-    const uint32_t b = i < n ? (uint32_t)cnt[i] : 0xffu;
-    uint32_t rank;
-    warp_bucket_counts(b, wc, rank);
-    __syncthreads();
-    if (threadIdx.x < kBuckets) {
-        uint32_t s = 0;
-        for (int w = 0; w < kSortWarps; ++w) s += wc[w][threadIdx.x];
-        blk_hist[(uint64_t)threadIdx.x * nblk + blockIdx.x] = s;
+    const uint32_t b = i < n ? (uint32_t)in.cnt[i] : 0xffu;
+    // paths without a collision are counted (bucket 0 of the table) but not stored
+    const unsigned zeros = __ballot_sync(0xffffffffu, b == 0u);
+    if ((threadIdx.x & 31) == 0 && zeros) atomicAdd(n_zero, (uint32_t)__popc(zeros));
+    if (i >= n) return;
+    uint32_t key = kNoKey;
+    if (b >= 1 && b < (uint32_t)n_buckets) {
+        const uint32_t pv = in.rec_a[in.stride + i].w & kVoxMask;
+        const uint32_t m = (spread3(pv & 511u) | (spread3((pv >> 9) & 511u) << 1) | (spread3((pv >> 18) & 511u) << 2))
+                           >> key_shift;
+        key = b * kPathBins + min(m, kPathBins - 1u);
+        atomicAdd(hist + key, 1u);
     }
+    keys[i] = key;
 }
 
-// exclusive scan of one bucket's per-block counts (in place); count -> Buckets
-__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ blk_hist, uint32_t nblk,
-                                                    Buckets* __restrict__ bk) {
-    __shared__ uint64_t part[1024];
-    uint32_t* h = blk_hist + (uint64_t)blockIdx.x * nblk;
-    const uint32_t chunk = (nblk + 1023) / 1024;
-    const uint32_t a = threadIdx.x * chunk, e = min(a + chunk, nblk);
-    uint64_t s = 0;
-    for (uint32_t j = a; j < e; ++j) s += h[j];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const uint64_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    uint64_t run = part[threadIdx.x] - s;   // exclusive prefix of this chunk
-    for (uint32_t j = a; j < e; ++j) {
-        const uint32_t v = h[j];
-        h[j] = (uint32_t)run;
-        run += v;
-    }
-    if (threadIdx.x == 1023) bk->count[blockIdx.x] = part[1023];
-}
-
-__global__ void k_bucket_offsets(Buckets* bk, int n_buckets) {
+// bucket table from the scanned key bins: bucket b's paths are the bins
+// [b kPathBins, (b + 1) kPathBins), in order
+__global__ void k_bucket_offsets(const uint32_t* __restrict__ hist, const uint32_t* __restrict__ cursor,
+                                 const uint32_t* __restrict__ n_zero, Buckets* bk, int n_buckets) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint32_t last = kSortBins - 1;
+    const uint64_t total = (uint64_t)cursor[last] + hist[last];
     uint64_t p = 0, r = 0, ev = 0;
     for (int b = 0; b < kBuckets; ++b) {
-        const uint64_t n = (b >= 1 && b < n_buckets) ? bk->count[b] : 0;   // B = 0 paths are not stored
-        if (b >= n_buckets) bk->count[b] = 0;
+        const uint64_t hi = b + 1 < kBuckets ? cursor[(b + 1) * kPathBins] : total;
+        const uint64_t n = (b >= 1 && b < n_buckets) ? hi - cursor[b * kPathBins] : 0;   // B = 0 paths are not stored
+        bk->count[b] = b == 0 ? *n_zero : n;
         bk->path_off[b] = p;
         bk->rec_off[b] = r;
         p += n;
@@ -94,31 +75,20 @@ __global__ void k_bucket_offsets(Buckets* bk, int n_buckets) {
     bk->n_events = ev;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(StoreBuf in, uint64_t n, const uint32_t* __restrict__ blk_off,
-                                                               uint32_t nblk, const Buckets* __restrict__ bk,
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(StoreBuf in, uint64_t n, const uint32_t* __restrict__ keys,
+                                                               uint32_t* __restrict__ cursor,
+                                                               const Buckets* __restrict__ bk,
                                                                uint4* __restrict__ out_a, float4* __restrict__ out_b,
                                                                const uint32_t* __restrict__ abort) {
-    if (abort && *abort) return;   // block-uniform: the store did not fit (nothing is written)
-    __shared__ uint32_t wc[kSortWarps][kBuckets];
-    __shared__ uint32_t wp[kSortWarps][kBuckets];
-    for (int k = threadIdx.x; k < kSortWarps * kBuckets; k += blockDim.x) (&wc[0][0])[k] = 0;
-    __syncthreads();
+    if (abort && *abort) return;   // the store did not fit (nothing is written)
     const uint64_t i = (uint64_t)blockIdx.x * kSortThreads + threadIdx.x;
-    const uint32_t b = i < n ? (uint32_t)in.cnt[i] : 0xffu;
-    uint32_t rank;
-    warp_bucket_counts(b, wc, rank);
-    __syncthreads();
-    if (threadIdx.x < kBuckets) {
-        uint32_t run = 0;
-        for (int w = 0; w < kSortWarps; ++w) {
-            wp[w][threadIdx.x] = run;
-            run += wc[w][threadIdx.x];
-        }
-    }
-    __syncthreads();
-    if (i >= n || b == 0 || b >= (uint32_t)kBuckets) return;
-    const uint64_t pos = (uint64_t)blk_off[(uint64_t)b * nblk + blockIdx.x] + wp[threadIdx.x >> 5][b] + rank;
+    if (i >= n) return;
+    const uint32_t key = keys[i];
+    if (key == kNoKey) return;
+    const uint32_t b = key / kPathBins;
+    const uint64_t pos = (uint64_t)atomicAdd(cursor + key, 1u) - bk->path_off[b];
     const uint64_t cb = bk->count[b], ro = bk->rec_off[b];
+    if (pos >= cb) return;   // (cannot happen: the key was counted)
     for (uint32_t k = 0; k <= b; ++k) {
         const uint64_t src = (uint64_t)k * in.stride + i;
         const uint64_t dst = ro + (uint64_t)k * cb + pos;
@@ -221,18 +191,32 @@ unsigned blocks_for(uint64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); 
 
 }  // namespace
 
-void launch_sort_count(const StoreBuf& in, uint64_t n, int n_buckets, uint32_t* blk_hist, Buckets* buckets,
-                       cudaStream_t st) {
-    const uint32_t nblk = blocks_for(n, kSortThreads);
-    k_sort_count<<<nblk, kSortThreads, 0, st>>>(in.cnt, n, blk_hist, nblk);
-    k_sort_scan<<<kBuckets, 1024, 0, st>>>(blk_hist, nblk, buckets);
-    k_bucket_offsets<<<1, 32, 0, st>>>(buckets, n_buckets);
+SortScratch sort_scratch(uint32_t* base, uint64_t n) {
+    SortScratch s;
+    s.keys = base;
+    s.hist = base + n;
+    s.cursor = s.hist + kSortBins;
+    s.partial = s.cursor + kSortBins;
+    s.n_zero = s.partial + 3 * 4096;
+    return s;
 }
 
-void launch_sort_scatter(const StoreBuf& in, uint64_t n, const uint32_t* blk_hist, Buckets* buckets, uint4* out_a,
+uint64_t sort_scratch_words(uint64_t n) { return n + 2ull * kSortBins + 3ull * 4096 + 1; }
+
+void launch_sort_count(const StoreBuf& in, uint64_t n, int n_buckets, int key_shift, const SortScratch& w,
+                       Buckets* buckets, cudaStream_t st) {
+    cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * kSortBins, st);
+    cudaMemsetAsync(w.n_zero, 0, sizeof(uint32_t), st);
+    const unsigned g = blocks_for(n, kSortThreads);
+    if (g) k_sort_keys<<<g, kSortThreads, 0, st>>>(in, n, n_buckets, key_shift, w.keys, w.hist, w.n_zero);
+    launch_scan(w.hist, w.cursor, w.partial, kSortBins, st);
+    k_bucket_offsets<<<1, 32, 0, st>>>(w.hist, w.cursor, w.n_zero, buckets, n_buckets);
+}
+
+void launch_sort_scatter(const StoreBuf& in, uint64_t n, const SortScratch& w, Buckets* buckets, uint4* out_a,
                          float4* out_b, cudaStream_t st, const uint32_t* abort) {
-    const uint32_t nblk = blocks_for(n, kSortThreads);
-    k_sort_scatter<<<nblk, kSortThreads, 0, st>>>(in, n, blk_hist, nblk, buckets, out_a, out_b, abort);
+    const unsigned g = blocks_for(n, kSortThreads);
+    if (g) k_sort_scatter<<<g, kSortThreads, 0, st>>>(in, n, w.keys, w.cursor, buckets, out_a, out_b, abort);
 }
 
 namespace {
@@ -256,8 +240,6 @@ void launch_store_guard(Buckets* buckets, uint64_t rec_cap, uint64_t ev_cap, con
                         int* err, cudaStream_t st) {
     k_store_guard<<<1, 32, 0, st>>>(buckets, rec_cap, ev_cap, bad, abort, err);
 }
-
-uint64_t sort_blocks(uint64_t n) { return blocks_for(n, kSortThreads); }
 
 void launch_grad_reference(const DevScene& S, const SortedPaths& P, const float* beta_t, const float* beta_ref,
                            const float* dbeta, const double* dldi, double* grad, cudaStream_t st) {
