@@ -18,11 +18,12 @@ import torch
 from . import native as N
 
 # kernels of this library launched per call (for launch accounting; memsets
-# are not counted): store = sample + 4 sort + 5 event-binning kernels,
+# are not counted): store = extinction check + sample + 6 path-sort kernels
+# (keys, three-level scan, bucket table, scatter) + 5 event-binning kernels,
 # reweight = delta + path weights + event forward, cached gradient = event
 # gradient + path gradient, uncached = delta + per-path gradient, counted
 # Adam = step counter + update (batched passes: native.Batch.kernels_per_step)
-LAUNCHES = {"store": 10, "reweight": 3, "residual": 1, "grad_cache": 2, "grad": 2, "adam": 1,
+LAUNCHES = {"store": 13, "reweight": 3, "residual": 1, "grad_cache": 2, "grad": 2, "adam": 1,
             "adam_counted": 2}
 
 
