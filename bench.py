@@ -562,7 +562,8 @@ def run_ablation(args, ws, rank, local):
 
 def run_recon(args, ws, rank, local):
     """The reconstruction of Sec. 6 on the 32^3 blob field (9 cameras at
-    64x64 pixels): hull carved at --recon-carve (0.2) of the mean lit pixel,
+    64x64 pixels; --recon-config noise128: the 128^3 noise field with its 15
+    cameras at 128x128): hull carved at --recon-carve (0.2) of the mean lit pixel,
     then Alg. 2 with 2^26 paths per step (2048 per voxel; --paths; the
     decorrelated gradient, hull only, N_r = 10), step max/100 (--recon-lr-div)
     decaying as 1/(1 + k/30) (--recon-decay), --recon-steps Adam steps;
@@ -579,10 +580,11 @@ def run_recon(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     n = args.paths or (1 << 26)
-    sc = synth.config(1, n_paths=n)
+    cfg, px = {"blobs32": (1, 64), "noise128": (3, 128)}[args.recon_config]
+    sc = synth.config(cfg, n_paths=n)
     bt = torch.from_numpy(sc.beta_cloud.reshape(-1).astype(np.float32)).cuda()
     steps = int(args.recon_steps)
-    c2f = CoarseToFine(sc, bt, levels=[(64, n)], n_r=N_R, lr=float(bt.max()) / args.recon_lr_div,
+    c2f = CoarseToFine(sc, bt, levels=[(px, n)], n_r=N_R, lr=float(bt.max()) / args.recon_lr_div,
                        carve_frac=args.recon_carve, min_gain=-1e9, max_steps_per_level=steps,
                        lr_decay=args.recon_decay, seed=sc.seed + rank)
     try:
@@ -633,7 +635,10 @@ def run_recon(args, ws, rank, local):
     out = {"metric": METRIC, "value": ws * paths / (step_ms * 1e-3), "unit": UNIT, "n_gpus": ws,
            "steps": len(hist), "warmup": 0, "ms_per_step": step_ms / len(hist), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"recon: 32^3 blobs (peak 20/km), 9 cameras at 64x64, hull carved at "
+           "config": {"workload": (f"recon: 32^3 blobs (peak 20/km), 9 cameras at 64x64, hull carved at "
+                                   if args.recon_config == "blobs32" else
+                                   f"recon: 128^3 thresholded noise (max 60/km), 15 cameras at 128x128, hull "
+                                   f"carved at ") +
                                   f"{args.recon_carve:g} of the mean lit pixel, {n} paths per step, N_r=10, "
                                   f"decorrelated gradient, step max/{args.recon_lr_div:g} / (1 + k/"
                                   f"{args.recon_decay:g}), {steps} steps",
@@ -1080,6 +1085,9 @@ def main():
     ap.add_argument("--recon-lr-div", type=float, default=100.0, help="recon workload: step = max extinction / this")
     ap.add_argument("--recon-decay", type=float, default=30.0,
                     help="recon workload: step decay 1/(1 + k/this); 0 = constant step")
+    ap.add_argument("--recon-config", default="blobs32", choices=["blobs32", "noise128"],
+                    help="recon workload: the field reconstructed (cameras at 64x64 for blobs32, 128x128 for "
+                         "noise128)")
     ap.add_argument("--recon-snr", action="store_true",
                     help="recon workload: first measure the start state's gradient cosine to a reference")
     ap.add_argument("--path-scale", type=int, default=0, help="batch workload: lower every 2^k path budget by k")
