@@ -1033,7 +1033,7 @@ def run_native(args, ws, rank, local):
         "config": {"workload": CONFIGS[args.workload][1], "n_paths": n, "n_r": N_R,
                    "parallelism": (f"paths sharded over {ws} ranks ({ws * n} paths per optimisation, "
                                    f"{args.shard_backend} all-reduce of images and gradient)") if shard
-                                  else f"{ws} independent replicas",
+                                  else (f"{ws} independent replicas" if ws > 1 else "one GPU"),
                    "lean_cache": bool(args.lean and n > (1 << 26)),
                    "accumulation": "f64 pixel and gradient sums",
                    "l2": "inputs larger than L2 (stored paths and contribution cache, GBs per step)",
