@@ -146,8 +146,10 @@ int render_forward(const pt_scene* scene, const float* beta_cloud,
  * paths_store -- sample, sort and store light paths (Alg. 2, the resample
  * branch: sample under M_t, sort by path size, set M_ref <- M_t).
  * Traces the same paths as render_forward would and keeps every path with at
- * least one collision, counting-sorted by its number of collisions B
- * (stable in path id), as compact vertex records.  The handle keeps a copy
+ * least one collision, counting-sorted by its number of collisions B and,
+ * among paths of one size, by the Morton code of its first collision's voxel
+ * (4096 bins; the order inside a bin is not fixed), as compact vertex
+ * records.  The handle keeps a copy
  * of beta_cloud as M_ref.  *paths == NULL creates a handle (owned by the
  * caller, freed with paths_free); an existing handle of the same scene is
  * reused.  images_ref (nullable) receives the plain estimate under M_ref (as
